@@ -1,0 +1,164 @@
+"""Pins of the oracle's Monte Carlo dynamics against closed forms and
+invariants: the Drude response of a constant-rate elastic isotropic scatterer,
+the Kane-Maxwellian equilibrium at zero field, the equilibrium valley ratio,
+energy conservation between field work and phonon emission, and exact integer
+particle conservation in the nanowire with its contacts.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import constants as sc
+from scipy import integrate
+
+import workloads as W
+
+Q, HB, KB, M0 = sc.e, sc.hbar, sc.k, sc.m_e
+
+
+def kane_mean_energy(T, alpha_eV, dEc=0.0):
+    kT = KB * T
+    a = alpha_eV / Q
+    g = lambda e: math.sqrt(e * (1 + a * e)) * (1 + 2 * a * e) * math.exp(-e / kT)
+    num = integrate.quad(lambda e: e * g(e), 0, 80 * kT, epsabs=0, epsrel=1e-12)[0]
+    den = integrate.quad(g, 0, 80 * kT, epsabs=0, epsrel=1e-12)[0]
+    return num / den
+
+
+def test_drude_response_constant_rate(oracle_mod):
+    """Constant rate G, elastic, isotropic, parabolic: <v(t)> = v0 e^{-Gt} -
+    (qF/mG)(1 - e^{-Gt}) and d<E>/dt = -qF <v> hold exactly in expectation."""
+    G, F, N = 1.0e13, 1.0e6, 40_000
+    c = W.bulk(n_particles=N, field_V_m=F, mech_mask=1 << 3, const_rate=G,
+               alpha_per_eV=(0.0, 0.0, 0.0), seed=3)
+    s = oracle_mod.Sim(c)
+    m = c["m_rel"][0] * M0
+    p0 = s.particles()
+    v0 = HB * p0["k"][:, 2].mean() / m
+    E0 = (HB ** 2 * (p0["k"] ** 2).sum(1) / (2 * m)).mean()
+    dt, prev = c["dt"], s.tallies()
+    step = 0
+    for blk in range(6):
+        n = 100
+        s.run(n)
+        cur = s.tallies()
+        ts = (step + np.arange(1, n + 1)) * dt
+        step += n
+        ex = np.exp(-G * ts)
+        want_v = np.mean(v0 * ex - Q * F / (m * G) * (1 - ex))
+        got_v = (cur["sum_v"][2] - prev["sum_v"][2]) / (n * N)
+        Emean = (cur["sum_E"] - prev["sum_E"]) / (n * N)
+        sig = math.sqrt(2.0 / 3.0 * Emean / m) / math.sqrt(N)
+        assert abs(got_v - want_v) < 5 * sig, (blk, got_v, want_v, sig)
+        want_E = np.mean(E0 - Q * F * (v0 * (1 - ex) / G - Q * F / (m * G) * (ts - (1 - ex) / G)))
+        assert Emean == pytest.approx(want_E, rel=0.01), (blk, Emean, want_E)
+        prev = cur
+    assert cur["events"][0, 0, 3] > 0 and cur["self_events"].sum() == 0
+
+
+def test_zero_field_equilibrium_mean_energy(oracle_mod):
+    c = W.bulk(n_particles=400_000, field_V_m=0.0, exact_rates=1, seed=11)
+    s = oracle_mod.Sim(c)
+    s.run(100)
+    ob = s.observables()
+    want = kane_mean_energy(300.0, c["alpha_per_eV"][0])
+    got = ob["E_mean_eV"] * Q
+    sem = 0.82 * want / math.sqrt(400_000)
+    assert abs(got - want) < 4 * sem, (got / Q, want / Q)
+    assert abs(got - 1.5 * KB * 300.0) > 4 * sem  # parabolic value is excluded
+    assert s.tallies()["overflow"] == 0
+
+
+def test_equilibrium_valley_ratio(oracle_mod):
+    """Synthetic U valley 0.1 eV above Gamma1 with fast intervalley coupling:
+    n_U / n_G1 = Z_U int g_U e^{-(E+dE)/kT} / int g_G1 e^{-E/kT}."""
+    T, dEc = 600.0, 0.1
+    c = W.bulk(n_particles=20_000, field_V_m=0.0, T=T, exact_rates=1, n_bins=512,
+               Ec_eV=(0.0, dEc, 2.1), hw_iv_eV=0.03, seed=5)
+    s = oracle_mod.Sim(c)
+    s.run(1000)
+    a = s.tallies()
+    s.run(800)
+    b = s.tallies()
+    occ = (b["valley_steps"] - a["valley_steps"]) / (b["n_samples"] - a["n_samples"])
+    kT = KB * T
+    def Zint(v, shift):
+        m = c["m_rel"][v] * M0
+        al = c["alpha_per_eV"][v] / Q
+        f = lambda e: m ** 1.5 * math.sqrt(e * (1 + al * e)) * (1 + 2 * al * e) * math.exp(-(e + shift) / kT)
+        return c["Z"][v] * integrate.quad(f, 0, 80 * kT, epsabs=0, epsrel=1e-12)[0]
+    want = Zint(1, dEc * Q) / Zint(0, 0.0)
+    got = occ[1] / occ[0]
+    assert got == pytest.approx(want, rel=0.03), (got, want)
+
+
+def test_energy_balance_bulk(oracle_mod):
+    """Sum over electrons of (kinetic + valley minimum) energy changes only by
+    field work -qF.v dt and by +-hw at each phonon absorption/emission."""
+    F = 1.0e7
+    c = W.bulk(n_particles=10_000, field_V_m=F, seed=2)
+    s = oracle_mod.Sim(c)
+    s.run(1)
+    t1 = s.tallies()
+    s.run(1500)
+    t2 = s.tallies()
+    s.run(1)
+    t3 = s.tallies()
+    E_start = t1["sum_Etot"]
+    E_end = t3["sum_Etot"] - t2["sum_Etot"]
+    dv = t3["sum_v"][2] - t1["sum_v"][2]
+    work = -Q * F * dv * c["dt"]
+    ev = t3["events"].astype(np.int64) - t1["events"].astype(np.int64)
+    net_pop = ev[..., 2].sum() - ev[..., 1].sum()
+    net_iv = ev[..., 5::2].sum() - ev[..., 4::2].sum()
+    emitted = net_pop * c["hw_lo_eV"] * Q + net_iv * c["hw_iv_eV"] * Q
+    assert (E_end - E_start) + emitted == pytest.approx(work, rel=0.01)
+    assert work > 0 and net_pop > 0
+
+
+def nanowire_small(**kw):
+    base = dict(n_particles=20_000, nx=20, Lx=200e-9, Vd=2.0, seed=9)
+    base.update(kw)
+    return W.nanowire(**base)
+
+
+def test_nanowire_conservation_and_contacts(oracle_mod):
+    c = nanowire_small()
+    s = oracle_mod.Sim(c)
+    s.run(120)
+    t = s.tallies()
+    cr = t["crossings"]
+    assert t["n_alive"] == c["n_particles"] - cr[0] - cr[1] + cr[2] + cr[3]
+    assert t["inject_starved"] == 0 and t["rejected"] == 0
+    p = s.particles()
+    al = p["alive"].astype(bool)
+    r = p["r"][al]
+    assert (r[:, 0] >= 0).all() and (r[:, 0] <= c["Lx"]).all()
+    assert (r[:, 1] >= 0).all() and (r[:, 1] <= c["Ly"]).all()
+    assert (r[:, 2] >= 0).all() and (r[:, 2] <= c["Lz"]).all()
+    ch = t["charge"].reshape(c["nx"], c["ny"], c["nz"])
+    assert ch.sum() == t["n_alive"]
+    Vcell = c["Lx"] * c["Ly"] * c["Lz"] / (c["nx"] * c["ny"] * c["nz"])
+    w = c["Nd"] * c["Lx"] * c["Ly"] * c["Lz"] / c["n_particles"]
+    target = round(c["Nd"] * Vcell / w)
+    assert (ch[0] >= target).all() and (ch[-1] >= target).all()
+    # electrons flow from source to drain at positive drain bias
+    assert cr[1] > cr[0]
+
+
+def test_deterministic_and_seeded(oracle_mod):
+    c = nanowire_small(n_particles=3000)
+    a = oracle_mod.Sim(c); a.run(30)
+    b = oracle_mod.Sim(c); b.run(30)
+    ta, tb = a.tallies(), b.tallies()
+    assert np.array_equal(ta["events"], tb["events"])
+    assert ta["sum_E"] == tb["sum_E"]
+    d = oracle_mod.Sim(W.copy_config(c, seed=10)); d.run(30)
+    assert not np.array_equal(ta["events"], d.tallies()["events"])
+
+
+def test_empty_ensemble(oracle_mod):
+    s = oracle_mod.Sim(W.bulk(n_particles=0))
+    s.run(5)
+    t = s.tallies()
+    assert t["n_samples"] == 0 and t["events"].sum() == 0 and t["steps_done"] == 5

@@ -1,0 +1,201 @@
+/*
+ * libemc: GB300 (sm_103a) ensemble electron Monte Carlo for wurtzite GaN.
+ *
+ * Hao et al., "Hybrid Electrothermal Simulation of a Three-Dimensional
+ * Fin-Shaped Field-Effect Transistor Based on GaN Nanowires" (arXiv:1707.09073).
+ * The paper's electron side: an ensemble Monte Carlo that tracks individual
+ * electrons (the paragraph opening "In such simulations"), Kane bands over the
+ * Gamma1/U/Gamma3 valleys with ionized impurity, polar optical, acoustic
+ * deformation potential and intervalley optical scattering and the Table I
+ * parameters (the paragraph opening "For Si-doped GaN nanowires"), a half
+ * nanowire divided into 3 x 6 x 100 subcells that count electrons for a
+ * Poisson update of the 3D field, and the electron-to-phonon energy exchange
+ * counted per subcell for the thermal side (the paragraph ending "for the
+ * following thermal simulations").
+ *
+ * Conventions for every entry point:
+ *  - Return EMC_OK or an error code; nothing throws.  emc_last_error() gives
+ *    the message of the last failure on a context.
+ *  - The context owns all device memory it allocates (cudaMalloc at init,
+ *    cudaFree at emc_destroy).  Caller pointers are never retained.
+ *  - Work is issued asynchronously on the CUDA stream given at init (NULL =
+ *    the legacy default stream).  Calls that copy results to the host
+ *    synchronise that stream.  Asynchronous CUDA errors surface as EMC_ECUDA
+ *    at the next call.
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - Units: SI in emc_config; results are documented per tally kind.
+ */
+#ifndef LIBEMC_EMC_H
+#define LIBEMC_EMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct emc_ctx emc_ctx;
+
+typedef enum emc_status {
+    EMC_OK = 0,
+    EMC_EINVAL = 1,     /* invalid argument or configuration */
+    EMC_ENOMEM = 2,     /* device or host allocation failed */
+    EMC_ECUDA = 3,      /* a CUDA call failed (message in emc_last_error) */
+    EMC_EOVERFLOW = 4,  /* a bounded loop or buffer limit was hit on the device */
+    EMC_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    EMC_ESTATE = 6      /* call not valid in the context's current state */
+} emc_status;
+
+enum { EMC_NV = 3, EMC_NM = 10 };
+enum { EMC_GEOM_BULK = 0, EMC_GEOM_NANOWIRE = 1 };
+enum { EMC_FP32 = 0, EMC_FP64 = 1 };
+
+/* Mechanism index m per valley (EMC_NM = 10):
+ *   0 ionized impurity (Brooks-Herring, elastic)
+ *   1 polar optical absorption, 2 polar optical emission
+ *   3 acoustic deformation potential (elastic, equipartition)
+ *   4+2j intervalley absorption into valley j, 5+2j emission into valley j
+ * Valleys: 0 Gamma1, 1 U, 2 Gamma3.  Self-scattering is counted apart. */
+
+/* One ensemble.  All ensembles of one context must agree on geometry, grid,
+ * precision, dt, n_bins, dE_eV and steps_per_poisson. */
+typedef struct emc_config {
+    /* Table I */
+    double m_rel[3];        /* valley-bottom effective mass / m0 */
+    double Ec_eV[3];        /* valley minima */
+    double alpha_per_eV[3]; /* Kane nonparabolicity */
+    double eps_s, eps_inf;  /* relative permittivities */
+    double rho_kg_m3;       /* mass density */
+    double Da_eV;           /* acoustic deformation potential */
+    double Dij_eV_per_m;    /* intervalley deformation potential */
+    /* readings of what the paper leaves open */
+    double hw_lo_eV;        /* polar optical phonon energy (91.2 meV in the text) */
+    double hw_iv_eV;        /* intervalley phonon energy */
+    double vs_m_s;          /* sound velocity for acoustic scattering */
+    /* operating point */
+    double T_K;             /* lattice temperature */
+    double Nd_m3;           /* ionized donors = electrons (full activation) */
+    double field_V_m[3];    /* uniform field, bulk geometry only */
+    double dt_s;            /* time step */
+    double dE_eV;           /* rate-table bin width */
+    double emax_init_kT;    /* truncation of the initial Kane-Maxwellian */
+    /* nanowire geometry (x along the wire, y across from symmetry plane A, z up) */
+    double Lx, Ly, Lz;      /* m */
+    double gate_x0, gate_x1;/* gated x range on the top and outer side faces */
+    double Vs, Vd, Vg;      /* terminal voltages */
+    double p_specular;      /* specular fraction on the outer side/top/bottom walls */
+    int64_t n_particles;    /* initial electrons (superparticles) */
+    int64_t capacity;       /* particle slots (>= n_particles; spare slots for injection) */
+    int32_t Z[3];           /* valley degeneracies */
+    int32_t geometry;       /* EMC_GEOM_BULK or EMC_GEOM_NANOWIRE */
+    int32_t n_bins;         /* rate-table bins (table spans [0, n_bins * dE_eV)) */
+    int32_t steps_per_poisson; /* nanowire: Poisson update every this many steps */
+    int32_t nx, ny, nz;     /* subcells */
+    int32_t gate_on;        /* 1: gate Dirichlet faces present */
+    uint32_t seed;          /* Philox key word 0 of this ensemble */
+    uint32_t mech_mask;     /* bit m set: mechanism m enabled */
+    int32_t precision;      /* EMC_FP32 (production) or EMC_FP64 (parity build) */
+    int32_t sort_period;    /* sort particles every this many launches (0 = never) */
+    int32_t block_size;     /* flight-kernel threads per block (0 = default 256) */
+    int32_t steps_per_launch; /* bulk: steps fused per flight launch (0 = default 50) */
+} emc_config;
+
+/* Per-ensemble observables accumulated over sampled particle-steps (every
+ * live particle is sampled at the end of every time step). */
+typedef struct emc_obs {
+    double sum_v[3];        /* group velocity, m/s */
+    double sum_E;           /* kinetic energy, J */
+    double sum_Etot;        /* kinetic + valley minimum, J */
+    int64_t n_samples;      /* particle-steps sampled */
+    int64_t valley_steps[3];/* particle-steps per valley */
+    int64_t self_events[3]; /* self-scatterings per valley */
+    int64_t overflow;       /* table lookups above the table range */
+    int64_t steps_done;     /* time steps since init */
+    int64_t n_alive;        /* live particles now */
+    int64_t inject_starved; /* injections skipped for lack of free slots */
+} emc_obs;
+
+/* Tally kinds for emc_tally (shapes per context with E ensembles, C cells;
+ * C = 1 for bulk): */
+enum {
+    EMC_TALLY_OBS = 0,       /* emc_obs[E] */
+    EMC_TALLY_EVENTS = 1,    /* uint64[E][3][10] real scattering events (valley, mechanism) */
+    EMC_TALLY_HEAT = 2,      /* int64[E][C][2] net phonon emissions (emitted - absorbed):
+                                [.][0] polar optical, [.][1] intervalley */
+    EMC_TALLY_CHARGE = 3,    /* int64[E][C] electrons per subcell at the last Poisson update
+                                (bulk: live electrons) */
+    EMC_TALLY_CROSSINGS = 4, /* int64[E][4] source out, drain out, source in, drain in */
+    EMC_TALLY_PHI = 5,       /* double[E][C] potential, V */
+    EMC_TALLY_FIELD = 6,     /* double[E][C][3] field, V/m */
+    EMC_TALLY_HEAT_J = 7     /* double[E][C] net energy emitted to phonons per subcell, J
+                                (superparticle weight included) */
+};
+
+/* Create a context holding one ensemble (emc_batch_init with n_ens = 1).
+ * Builds the FP64 rate tables, draws the initial Kane-Maxwellian ensemble
+ * from Philox key (seed, particle id), and for the nanowire assembles the
+ * Poisson operator and solves for the initial field.  cuda_stream is a
+ * cudaStream_t (NULL = default stream).  *out receives the context. */
+emc_status emc_init(const emc_config* cfg, void* cuda_stream, emc_ctx** out);
+
+/* Create a context holding n_ens independent ensembles (bias points,
+ * temperatures, dopings, sizes) simulated together by every launch. */
+emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* cuda_stream, emc_ctx** out);
+
+/* Advance every ensemble by n_steps time steps of dt (asynchronous on the
+ * context stream).  Per step and particle: free flight under the field with
+ * Kane dispersion, self-scattering against Gamma0, choice of mechanism and
+ * final state, nanowire walls and contacts; tallies are accumulated.  In the
+ * nanowire, every steps_per_poisson steps the contact subcells are refilled,
+ * the subcell charge is counted and the FP64 Poisson update recomputes the
+ * field.  n_steps < 0 is EMC_EINVAL; 0 is a no-op. */
+emc_status emc_step(emc_ctx* ctx, int32_t n_steps);
+
+/* Copy tally `kind` (EMC_TALLY_*) of every ensemble into dst (bytes must be
+ * at least the size given above; dst_is_device: 1 = device pointer on the
+ * context's device, 0 = host).  Synchronises the context stream.  reset = 1
+ * zeroes the accumulating tallies (OBS sums and counts except steps_done and
+ * n_alive, EVENTS, HEAT, CROSSINGS) after the copy. */
+emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes,
+                     int32_t dst_is_device, int32_t reset);
+
+/* FP64 Poisson solve on the context's subcell grid (nanowire only), for
+ * ensemble 0 of the context:  div(eps_s eps0 grad phi) = -rho with the
+ * Dirichlet terminal faces at bc_volts = {Vs, Vd, Vg}.  charge_or_null: host
+ * double[C] charge density in C/m^3, or NULL to use the current subcell
+ * electron count (rho = q (Nd - w n / V_cell)).  phi_out_or_null: host
+ * double[C] receives phi (V).  Does not change the context's field. */
+emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null,
+                         const double* bc_volts, double* phi_out_or_null);
+
+/* Set the terminal voltages of ensemble ens and re-solve its field. */
+emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg);
+
+/* Diagnostics used by the test-suite. */
+/* Philox4x32-10 evaluated on the device for n (counter, key) pairs:
+ * ctr[n][4], key[n][2] in, out[n][4] out (host arrays). */
+emc_status emc_debug_philox(emc_ctx* ctx, const uint32_t* ctr, const uint32_t* key,
+                            uint32_t* out, int32_t n);
+/* Particle state in slot order, host arrays of `capacity` rows (total over
+ * ensembles): k[.][3] (1/m), r[.][3] (m), tr (s), valley (-1 = no particle),
+ * ensemble, id, philox counter. */
+emc_status emc_debug_particles(emc_ctx* ctx, double* k, double* r, double* tr,
+                               int32_t* valley, int32_t* ens, uint32_t* id, uint64_t* ctr);
+/* Rate tables of ensemble ens as built on the device (double[3][n_bins][10],
+ * cumulative / Gamma0) and Gamma0 (double[3], 1/s). */
+emc_status emc_debug_tables(emc_ctx* ctx, int32_t ens, double* table, double* gamma0);
+
+/* Number of ensembles, total particle slots and subcells of a context. */
+emc_status emc_shape(const emc_ctx* ctx, int32_t* n_ens, int64_t* capacity, int32_t* n_cell);
+
+/* Kernel launches issued by this context since init (for accounting). */
+int64_t emc_launch_count(const emc_ctx* ctx);
+
+const char* emc_last_error(const emc_ctx* ctx);
+void emc_destroy(emc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

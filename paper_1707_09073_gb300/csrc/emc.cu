@@ -1,0 +1,1112 @@
+// libemc host side: the C ABI of include/emc.h, device memory, rate tables,
+// Poisson update and the step loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/emc.h"
+#include "common.cuh"
+
+namespace emc {
+template <typename Real> void launch_flight(const DevParams&, bool, int, int, int, cudaStream_t);
+template <typename Real> void launch_init(const DevParams&, bool, cudaStream_t);
+template <typename Real> void launch_inject(const DevParams&, cudaStream_t);
+template <typename Real> cudaError_t flight_set_smem(size_t);
+template <typename Real> size_t flight_smem_bytes(int);
+}  // namespace emc
+
+using namespace emc;
+
+namespace {
+
+constexpr int kPoissonSweeps = 4;
+constexpr size_t kSmemTableBudget = 96 * 1024;  // bytes of rate table staged per block
+constexpr int kMaxCells = 8192;                 // dense FP64 Poisson inverse limit
+
+// Golden-rule prefactors of one table set in device units (nm, fs, eV).
+struct RateConst {
+    double ck[NV], alpha[NV], Ec[NV];
+    double hw_lo, hw_iv, N_lo, N_iv;
+    double pop_K;   // (e^2/eps0) hw_lo (1/eps_inf - 1/eps_s) / 2        eV^2 nm
+    double ac_K;    // Da^2 kT / (rho vs^2)                               eV^2 nm^3
+    double iv_K;    // hbar^2 Dij^2 / (2 rho hw_iv)                       eV^2 nm^3
+    double imp_K;   // N_I (e^2 / (eps_s eps0))^2                         eV^2 / nm
+    double beta2;   // Debye screening wave vector^2                     1/nm^2
+    int Z[NV];
+    uint32_t mask;
+};
+
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct emc_ctx {
+    cudaStream_t st = nullptr;
+    std::vector<emc_config> cfg;
+    int n_ens = 0, prec = EMC_FP32, geom = EMC_GEOM_BULK;
+    int nx = 1, ny = 1, nz = 1, ncell = 1, nb = 0, n_tab = 0, block = 256, spl = 50, K = 10;
+    int sort_period = 0;
+    int64_t n_slots = 0, steps_done = 0, launches = 0;
+    double dt_fs = 1.0, dE = 0.002;
+    double Lx = 1, Ly = 1, Lz = 1, dx = 1, dy = 1, dz = 1;  // nm
+    std::vector<int64_t> off, cap, n0;
+    std::vector<int32_t> tabset;
+    std::vector<RateConst> rc;     // per table set
+    std::vector<double> w;         // superparticle weight per ensemble
+    std::vector<double> bias;      // [E][3] Vs Vd Vg
+    std::vector<double> g0_host;   // [TS][NV] Gamma0, 1/fs
+    std::vector<uint8_t> gate_ix;  // [nx]
+    std::string err;
+    DevParams P{};
+    // device buffers
+    void *kx = nullptr, *ky = nullptr, *kz = nullptr, *x = nullptr, *y = nullptr, *z = nullptr, *tr = nullptr;
+    uint32_t *tag = nullptr, *id = nullptr, *slot_of_id = nullptr, *dead_bits = nullptr;
+    uint64_t* ctr = nullptr;
+    int64_t *d_off = nullptr, *d_cap = nullptr, *d_n0 = nullptr, *d_bits_off = nullptr;
+    uint32_t* d_seed = nullptr;
+    int32_t *d_tabset = nullptr, *d_target = nullptr;
+    void *acc_bulk = nullptr, *acc_cell = nullptr, *table = nullptr, *phys = nullptr;
+    double* tab64 = nullptr;
+    unsigned long long *events = nullptr, *cnt = nullptr;
+    double* sums = nullptr;
+    long long* heat = nullptr;
+    int* charge = nullptr;
+    int* d_err = nullptr;
+    // Poisson
+    double *Lmat = nullptr, *Ginv = nullptr, *phi = nullptr, *rhs = nullptr, *Efield = nullptr, *d_bias = nullptr,
+           *d_w = nullptr, *d_Nd = nullptr;
+    float *G32 = nullptr, *r32 = nullptr;
+    uint8_t* d_gate = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+emc_status fail(emc_ctx* c, emc_status s, const std::string& m)
+{
+    if (c) c->err = m;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, EMC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(emc_ctx* ctx, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        ctx->allocs.push_back(q);
+        cudaMemsetAsync(q, 0, std::max<size_t>(n, 1) * sizeof(T), ctx->st);
+        *p = static_cast<T*>(q);
+    }
+    return e;
+}
+
+// --------------------------------------------------------------- rates
+__device__ double dos(const RateConst& R, int v, double E)
+{
+    const double g = E * (1.0 + R.alpha[v] * E);
+    return pow(1.0 / R.ck[v], 1.5) * sqrt(g) * (1.0 + 2.0 * R.alpha[v] * E) / (4.0 * kPi * kPi);
+}
+
+// total out-scattering rate (1/fs) of mechanism m in valley v at energy E (eV)
+__device__ double rate(const RateConst& R, int v, int m, double E)
+{
+    if (!((R.mask >> m) & 1u) || E < 0.0) return 0.0;
+    const double two_pi_hbar = 2.0 * kPi / kHbarEVfs;
+    if (m == 0) {
+        if (E <= 0.0) return 0.0;
+        const double k = sqrt(E * (1.0 + R.alpha[v] * E) / R.ck[v]);
+        const double k2dkdE = k * (1.0 + 2.0 * R.alpha[v] * E) / (2.0 * R.ck[v]);
+        return R.imp_K * k2dkdE / (kPi * kHbarEVfs * R.beta2 * (4.0 * k * k + R.beta2));
+    }
+    if (m == 1 || m == 2) {
+        const double Ep = (m == 1) ? E + R.hw_lo : E - R.hw_lo;
+        if (Ep <= 0.0) return 0.0;
+        const double occ = (m == 1) ? R.N_lo : R.N_lo + 1.0;
+        const double k = sqrt(E * (1.0 + R.alpha[v] * E) / R.ck[v]);
+        const double kp = sqrt(Ep * (1.0 + R.alpha[v] * Ep) / R.ck[v]);
+        const double Lk = (k > 0.0) ? log(fabs((k + kp) / (k - kp))) / k : 2.0 / kp;
+        return R.pop_K * occ * (1.0 + 2.0 * R.alpha[v] * Ep) * Lk / (4.0 * kPi * kHbarEVfs * R.ck[v]);
+    }
+    if (m == 3) return two_pi_hbar * R.ac_K * dos(R, v, E);
+    const int j = (m - 4) >> 1;
+    const bool absorb = (m & 1) == 0;
+    const int Zf = R.Z[j] - (j == v ? 1 : 0);
+    if (Zf <= 0) return 0.0;
+    const double Ep = E + (absorb ? R.hw_iv : -R.hw_iv) - (R.Ec[j] - R.Ec[v]);
+    if (Ep <= 0.0) return 0.0;
+    const double occ = absorb ? R.N_iv : R.N_iv + 1.0;
+    return two_pi_hbar * R.iv_K * Zf * occ * dos(R, j, Ep);
+}
+
+// cumulative rates at the lower edge of every bin: tab64[ts][v][b][m]
+__global__ void k_rates(const RateConst* rc, int n_tab, int nb, double dE, double* tab64)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_tab * NV * nb) return;
+    const int ts = int(i / (NV * nb));
+    const int v = int((i / nb) % NV);
+    const int b = int(i % nb);
+    const RateConst R = rc[ts];
+    const double E = b * dE;
+    double acc = 0.0;
+    double* row = tab64 + (size_t)i * NM;
+    for (int m = 0; m < NM; ++m) {
+        acc += rate(R, v, m, E);
+        row[m] = acc;
+    }
+}
+
+// Gamma0 = max over bins of the total; one block per (ts, v)
+__global__ void k_gamma0(const double* tab64, int nb, double* g0)
+{
+    __shared__ double red[256];
+    const double* base = tab64 + (size_t)blockIdx.x * nb * NM;
+    double mx = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) mx = fmax(mx, base[(size_t)b * NM + NM - 1]);
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) g0[blockIdx.x] = red[0];
+}
+
+template <typename Real>
+__global__ void k_normalise(double* tab64, const double* g0, int nb, int64_t n, Real* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t tv = i / ((int64_t)nb * NM);
+    const double g = g0[tv];
+    const double x = g > 0.0 ? tab64[i] / g : 0.0;
+    tab64[i] = x;
+    out[i] = Real(x);
+}
+
+// -------------------------------------------------------------- Poisson
+// L = -(7-point Laplacian) on cell centres (nm^-2), Dirichlet faces half a
+// cell away: source/drain x faces always, gate faces (outer side y = Ly and
+// top z = Lz) where the cell's x centre is gated.  Neumann elsewhere.
+__global__ void k_build_L(double* L, int nx, int ny, int nz, double ax, double ay, double az, const uint8_t* gate)
+{
+    const int n = nx * ny * nz;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int i = c / (ny * nz), j = (c / nz) % ny, l = c % nz;
+    double* row = L + (size_t)c * n;
+    double d = 0.0;
+    auto nb = [&](int cc, double a) {
+        row[cc] -= a;
+        d += a;
+    };
+    if (i > 0) nb(c - ny * nz, ax); else d += 2.0 * ax;
+    if (i < nx - 1) nb(c + ny * nz, ax); else d += 2.0 * ax;
+    if (j > 0) nb(c - nz, ay);
+    if (j < ny - 1) nb(c + nz, ay); else if (gate[i]) d += 2.0 * ay;
+    if (l > 0) nb(c - 1, az);
+    if (l < nz - 1) nb(c + 1, az); else if (gate[i]) d += 2.0 * az;
+    row[c] += d;
+}
+
+// one Gauss-Jordan pivot step of the in-place inversion (no pivoting: L is SPD)
+__global__ void k_gj(const double* A, double* B, int n, int k)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n) return;
+    const double p = 1.0 / A[(size_t)k * n + k];
+    double out;
+    if (i == k && j == k) out = p;
+    else if (i == k) out = A[(size_t)k * n + j] * p;
+    else if (j == k) out = -A[(size_t)i * n + k] * p;
+    else out = A[(size_t)i * n + j] - A[(size_t)i * n + k] * (A[(size_t)k * n + j] * p);
+    B[(size_t)i * n + j] = out;
+}
+
+__global__ void k_to_f32(const double* a, float* b, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = float(a[i]);
+}
+
+struct PoisGeo {
+    int nx, ny, nz, n;
+    double ax, ay, az;
+    const uint8_t* gate;
+};
+
+// rhs = rho / (eps_s eps0) + Dirichlet face terms (V/nm^2).  rho from the
+// subcell count (charge != null) or from a given density rho_in (C/m^3).
+__global__ void k_rhs(PoisGeo G, int n_ens, const int* charge, const double* rho_in, const double* w,
+                      const double* Nd_nm, double Vcell, double e2eps, const double* bias, double* rhs)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_ens * G.n) return;
+    const int e = int(i / G.n), c = int(i % G.n);
+    const int ix = c / (G.ny * G.nz), iy = (c / G.nz) % G.ny, iz = c % G.nz;
+    double r;
+    if (charge) r = e2eps * (Nd_nm[e] - w[e] * charge[i] / Vcell);
+    else r = e2eps * rho_in[c] / kQ * 1e-27;
+    const double* B = bias + 3 * e;
+    if (ix == 0) r += 2.0 * G.ax * B[0];
+    if (ix == G.nx - 1) r += 2.0 * G.ax * B[1];
+    if (G.gate[ix]) {
+        if (iy == G.ny - 1) r += 2.0 * G.ay * B[2];
+        if (iz == G.nz - 1) r += 2.0 * G.az * B[2];
+    }
+    rhs[i] = r;
+}
+
+// residual r = rhs - L phi in FP64 (stencil), stored as float for the sweep
+__global__ void k_resid(PoisGeo G, int n_ens, const double* rhs, const double* phi, float* r32)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_ens * G.n) return;
+    const int e = int(i / G.n), c = int(i % G.n);
+    const int ix = c / (G.ny * G.nz), iy = (c / G.nz) % G.ny, iz = c % G.nz;
+    const double* p = phi + (size_t)e * G.n;
+    const double pc = p[c];
+    double acc = 0.0;
+    const int sx = G.ny * G.nz, sy = G.nz;
+    acc += (ix > 0) ? G.ax * (pc - p[c - sx]) : 2.0 * G.ax * pc;
+    acc += (ix < G.nx - 1) ? G.ax * (pc - p[c + sx]) : 2.0 * G.ax * pc;
+    if (iy > 0) acc += G.ay * (pc - p[c - sy]);
+    if (iy < G.ny - 1) acc += G.ay * (pc - p[c + sy]);
+    else if (G.gate[ix]) acc += 2.0 * G.ay * pc;
+    if (iz > 0) acc += G.az * (pc - p[c - 1]);
+    if (iz < G.nz - 1) acc += G.az * (pc - p[c + 1]);
+    else if (G.gate[ix]) acc += 2.0 * G.az * pc;
+    r32[i] = float(rhs[i] - acc);
+}
+
+// phi[e] += Ginv r[e]: one warp per row, 8 ensembles per block column
+__global__ void k_sweep(const float* G32, const float* r32, double* phi, int n, int n_ens)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int e0 = blockIdx.y * 8;
+    if (row >= n) return;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float* g = G32 + (size_t)row * n;
+    for (int j = lane; j < n; j += 32) {
+        const float gj = g[j];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (e0 + c < n_ens) acc[c] += gj * r32[(size_t)(e0 + c) * n + j];
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0 && e0 + c < n_ens) phi[(size_t)(e0 + c) * n + row] += double(v);
+    }
+}
+
+// E = -grad phi (V/nm): central differences, one-sided in boundary cells.
+template <typename Real>
+__global__ void k_field(PoisGeo G, int n_ens, const double* phi, double hx, double hy, double hz, double* Efield,
+                        Real* acc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_ens * G.n) return;
+    const int e = int(i / G.n), c = int(i % G.n);
+    const int idx[3] = {c / (G.ny * G.nz), (c / G.nz) % G.ny, c % G.nz};
+    const int nn[3] = {G.nx, G.ny, G.nz};
+    const int st[3] = {G.ny * G.nz, G.nz, 1};
+    const double h[3] = {hx, hy, hz};
+    const double* p = phi + (size_t)e * G.n;
+    for (int a = 0; a < 3; ++a) {
+        double g;
+        if (nn[a] == 1) g = 0.0;
+        else if (idx[a] == 0) g = (p[c + st[a]] - p[c]) / h[a];
+        else if (idx[a] == nn[a] - 1) g = (p[c] - p[c - st[a]]) / h[a];
+        else g = (p[c + st[a]] - p[c - st[a]]) / (2.0 * h[a]);
+        const double E = -g;                        // V/nm
+        Efield[i * 3 + a] = E * 1e9;                // V/m
+        acc[i * 3 + a] = Real(-E / kHbarEVfs);      // dk/dt of an electron, 1/(nm fs)
+    }
+}
+
+__global__ void k_count_alive(const uint32_t* tag, int64_t n, unsigned long long* cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = tag[i];
+    if ((t & 0xFFu) != DEAD) atomicAdd(&cnt[(size_t)(t >> 8)], 1ull);
+}
+
+__global__ void k_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    U4 c{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    U4 r = philox10(c, key[2 * i], key[2 * i + 1]);
+    out[4 * i] = r.a;
+    out[4 * i + 1] = r.b;
+    out[4 * i + 2] = r.c;
+    out[4 * i + 3] = r.d;
+}
+
+// ------------------------------------------------------------ helpers
+unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+bool same_table(const emc_config& a, const emc_config& b)
+{
+    for (int i = 0; i < 3; ++i)
+        if (a.m_rel[i] != b.m_rel[i] || a.Ec_eV[i] != b.Ec_eV[i] || a.alpha_per_eV[i] != b.alpha_per_eV[i] ||
+            a.Z[i] != b.Z[i])
+            return false;
+    return a.eps_s == b.eps_s && a.eps_inf == b.eps_inf && a.rho_kg_m3 == b.rho_kg_m3 && a.Da_eV == b.Da_eV &&
+           a.Dij_eV_per_m == b.Dij_eV_per_m && a.hw_lo_eV == b.hw_lo_eV && a.hw_iv_eV == b.hw_iv_eV &&
+           a.vs_m_s == b.vs_m_s && a.T_K == b.T_K && a.Nd_m3 == b.Nd_m3 && a.mech_mask == b.mech_mask &&
+           a.emax_init_kT == b.emax_init_kT;
+}
+
+RateConst make_rc(const emc_config& c)
+{
+    RateConst R{};
+    const double kT = kKB * c.T_K / kQ;  // eV
+    for (int v = 0; v < NV; ++v) {
+        R.ck[v] = kCk0 / c.m_rel[v];
+        R.alpha[v] = c.alpha_per_eV[v];
+        R.Ec[v] = c.Ec_eV[v];
+        R.Z[v] = c.Z[v];
+    }
+    R.hw_lo = c.hw_lo_eV;
+    R.hw_iv = c.hw_iv_eV;
+    R.N_lo = 1.0 / std::expm1(c.hw_lo_eV / kT);
+    R.N_iv = 1.0 / std::expm1(c.hw_iv_eV / kT);
+    const double rho_vs2 = c.rho_kg_m3 * c.vs_m_s * c.vs_m_s / kQ * 1e-27;  // eV/nm^3
+    const double rho_s = c.rho_kg_m3 * 1e-15 / kQ;                           // eV fs^2/nm^5
+    const double D = c.Dij_eV_per_m * 1e-9;                                  // eV/nm
+    const double Nd_nm = c.Nd_m3 * 1e-27;
+    const double e2es = kE2Eps0 / c.eps_s;                                   // eV nm
+    R.pop_K = kE2Eps0 * c.hw_lo_eV * (1.0 / c.eps_inf - 1.0 / c.eps_s) / 2.0;
+    R.ac_K = c.Da_eV * c.Da_eV * kT / rho_vs2;
+    R.iv_K = kHbarEVfs * kHbarEVfs * D * D / (2.0 * rho_s * c.hw_iv_eV);
+    R.imp_K = Nd_nm * e2es * e2es;
+    R.beta2 = e2es * Nd_nm / kT;
+    R.mask = c.mech_mask;
+    return R;
+}
+
+template <typename Real>
+Phys<Real> make_phys(const emc_config& c, const RateConst& R, const double* g0)
+{
+    Phys<Real> p{};
+    const double kT = kKB * c.T_K / kQ;
+    for (int v = 0; v < NV; ++v) {
+        p.ck[v] = Real(R.ck[v]);
+        p.vk[v] = Real(kVk0 / c.m_rel[v]);
+        p.alpha[v] = Real(c.alpha_per_eV[v]);
+        p.Ec[v] = Real(c.Ec_eV[v]);
+        p.inv_g0[v] = Real(g0[v] > 0.0 ? 1.0 / g0[v] : 0.0);
+    }
+    p.hw_lo = Real(c.hw_lo_eV);
+    p.hw_iv = Real(c.hw_iv_eV);
+    p.beta2 = Real(R.beta2);
+    p.kT = Real(kT);
+    const double emax = c.emax_init_kT * kT;
+    p.emax_init = Real(emax);
+    const double a = c.alpha_per_eV[0];
+    p.hmax0 = Real(std::sqrt(1.0 + a * emax) * (1.0 + 2.0 * a * emax));
+    return p;
+}
+
+emc_status validate(const emc_config* c, int n, emc_ctx* ctx)
+{
+    if (!c || n <= 0) return fail(ctx, EMC_EINVAL, "no configuration");
+    if (n > (1 << 24) - 1) return fail(ctx, EMC_EINVAL, "too many ensembles");
+    const emc_config& a = c[0];
+    for (int e = 0; e < n; ++e) {
+        const emc_config& b = c[e];
+        if (b.geometry != a.geometry || b.precision != a.precision || b.dt_s != a.dt_s || b.n_bins != a.n_bins ||
+            b.dE_eV != a.dE_eV || b.steps_per_poisson != a.steps_per_poisson || b.nx != a.nx || b.ny != a.ny ||
+            b.nz != a.nz || b.Lx != a.Lx || b.Ly != a.Ly || b.Lz != a.Lz || b.gate_on != a.gate_on ||
+            b.gate_x0 != a.gate_x0 || b.gate_x1 != a.gate_x1 || b.eps_s != a.eps_s)
+            return fail(ctx, EMC_EINVAL, "ensembles of one context must share geometry, grid, precision, dt, table");
+        if (b.n_particles < 0 || b.capacity < b.n_particles || b.capacity > 0x7FFFFFFF)
+            return fail(ctx, EMC_EINVAL, "need 0 <= n_particles <= capacity < 2^31");
+        if (!(b.T_K > 0) || !(b.Nd_m3 > 0) || !(b.dt_s > 0) || !(b.dE_eV > 0) || b.n_bins <= 0)
+            return fail(ctx, EMC_EINVAL, "T, Nd, dt, dE and n_bins must be positive");
+        for (int v = 0; v < 3; ++v)
+            if (!(b.m_rel[v] > 0) || b.alpha_per_eV[v] < 0 || b.Z[v] < 0)
+                return fail(ctx, EMC_EINVAL, "invalid valley parameters");
+        if (!(b.eps_s > b.eps_inf) || !(b.eps_inf > 0) || !(b.rho_kg_m3 > 0) || !(b.vs_m_s > 0) ||
+            !(b.hw_lo_eV > 0) || !(b.hw_iv_eV > 0))
+            return fail(ctx, EMC_EINVAL, "invalid material parameters");
+        if (b.precision != EMC_FP32 && b.precision != EMC_FP64) return fail(ctx, EMC_EINVAL, "precision");
+        if (b.geometry == EMC_GEOM_NANOWIRE) {
+            if (b.nx < 2 || b.ny < 1 || b.nz < 1 || (int64_t)b.nx * b.ny * b.nz > kMaxCells)
+                return fail(ctx, EMC_EINVAL, "nanowire grid: nx >= 2, ny, nz >= 1, cells <= 8192");
+            if (!(b.Lx > 0 && b.Ly > 0 && b.Lz > 0) || b.steps_per_poisson <= 0)
+                return fail(ctx, EMC_EINVAL, "nanowire lengths and steps_per_poisson must be positive");
+            if (b.p_specular < 0 || b.p_specular > 1) return fail(ctx, EMC_EINVAL, "p_specular in [0,1]");
+        } else if (b.geometry != EMC_GEOM_BULK) {
+            return fail(ctx, EMC_EINVAL, "geometry");
+        }
+        if (b.block_size != 0 && (b.block_size < 32 || b.block_size > 512 || b.block_size % 32))
+            return fail(ctx, EMC_EINVAL, "block_size: multiple of 32 in [32, 512]");
+    }
+    return EMC_OK;
+}
+
+template <typename Real>
+emc_status build_tables_and_phys(emc_ctx* ctx)
+{
+    const int TS = ctx->n_tab, nb = ctx->nb;
+    RateConst* d_rc = nullptr;
+    double* d_g0 = nullptr;
+    CK(dalloc(ctx, &d_rc, TS));
+    CK(dalloc(ctx, &d_g0, (size_t)TS * NV));
+    CK(cudaMemcpyAsync(d_rc, ctx->rc.data(), sizeof(RateConst) * TS, cudaMemcpyHostToDevice, ctx->st));
+    const int64_t rows = (int64_t)TS * NV * nb;
+    CK(dalloc(ctx, &ctx->tab64, (size_t)rows * NM));
+    Real* tabR = nullptr;
+    CK(dalloc(ctx, &tabR, (size_t)rows * NM));
+    ctx->table = tabR;
+    k_rates<<<grid_for(rows, 128), 128, 0, ctx->st>>>(d_rc, TS, nb, ctx->dE, ctx->tab64);
+    k_gamma0<<<TS * NV, 256, 0, ctx->st>>>(ctx->tab64, nb, d_g0);
+    k_normalise<Real><<<grid_for(rows * NM, 256), 256, 0, ctx->st>>>(ctx->tab64, d_g0, nb, rows * NM, tabR);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    ctx->g0_host.assign((size_t)TS * NV, 0.0);
+    CK(cudaMemcpyAsync(ctx->g0_host.data(), d_g0, sizeof(double) * TS * NV, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<Phys<Real>> ph(TS);
+    std::vector<int> rep(TS, -1);
+    for (int e = 0; e < ctx->n_ens; ++e)
+        if (rep[ctx->tabset[e]] < 0) rep[ctx->tabset[e]] = e;
+    for (int t = 0; t < TS; ++t) {
+        for (int v = 0; v < NV; ++v)
+            if (!(ctx->g0_host[t * NV + v] > 0.0))
+                return fail(ctx, EMC_EINVAL, "a valley has zero total scattering rate (check mech_mask)");
+        ph[t] = make_phys<Real>(ctx->cfg[rep[t]], ctx->rc[t], &ctx->g0_host[t * NV]);
+    }
+    Phys<Real>* d_ph = nullptr;
+    CK(dalloc(ctx, &d_ph, TS));
+    CK(cudaMemcpyAsync(d_ph, ph.data(), sizeof(Phys<Real>) * TS, cudaMemcpyHostToDevice, ctx->st));
+    ctx->phys = d_ph;
+    return EMC_OK;
+}
+
+template <typename Real>
+emc_status alloc_particles(emc_ctx* ctx)
+{
+    const size_t n = (size_t)ctx->n_slots;
+    Real *a, *b, *c, *d, *e, *f, *g;
+    CK(dalloc(ctx, &a, n));
+    CK(dalloc(ctx, &b, n));
+    CK(dalloc(ctx, &c, n));
+    CK(dalloc(ctx, &g, n));
+    ctx->kx = a; ctx->ky = b; ctx->kz = c; ctx->tr = g;
+    if (ctx->geom == EMC_GEOM_NANOWIRE) {
+        CK(dalloc(ctx, &d, n));
+        CK(dalloc(ctx, &e, n));
+        CK(dalloc(ctx, &f, n));
+        ctx->x = d; ctx->y = e; ctx->z = f;
+    }
+    Real *ab = nullptr, *ac = nullptr;
+    CK(dalloc(ctx, &ab, (size_t)ctx->n_ens * 3));
+    CK(dalloc(ctx, &ac, (size_t)ctx->n_ens * ctx->ncell * 3));
+    ctx->acc_bulk = ab;
+    ctx->acc_cell = ac;
+    std::vector<Real> hb((size_t)ctx->n_ens * 3);
+    for (int e = 0; e < ctx->n_ens; ++e)
+        for (int i = 0; i < 3; ++i) hb[3 * e + i] = Real(-ctx->cfg[e].field_V_m[i] * 1e-9 / kHbarEVfs);
+    CK(cudaMemcpyAsync(ab, hb.data(), sizeof(Real) * hb.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+PoisGeo pgeo(const emc_ctx* ctx)
+{
+    PoisGeo G;
+    G.nx = ctx->nx;
+    G.ny = ctx->ny;
+    G.nz = ctx->nz;
+    G.n = ctx->ncell;
+    G.ax = 1.0 / (ctx->dx * ctx->dx);
+    G.ay = 1.0 / (ctx->dy * ctx->dy);
+    G.az = 1.0 / (ctx->dz * ctx->dz);
+    G.gate = ctx->d_gate;
+    return G;
+}
+
+emc_status poisson_setup(emc_ctx* ctx)
+{
+    const int n = ctx->ncell;
+    const size_t nn = (size_t)n * n;
+    CK(dalloc(ctx, &ctx->Lmat, nn));
+    CK(dalloc(ctx, &ctx->Ginv, nn));
+    CK(dalloc(ctx, &ctx->G32, nn));
+    CK(dalloc(ctx, &ctx->phi, (size_t)ctx->n_ens * n));
+    CK(dalloc(ctx, &ctx->rhs, (size_t)ctx->n_ens * n));
+    CK(dalloc(ctx, &ctx->r32, (size_t)ctx->n_ens * n));
+    CK(dalloc(ctx, &ctx->Efield, (size_t)ctx->n_ens * n * 3));
+    CK(dalloc(ctx, &ctx->d_gate, (size_t)ctx->nx));
+    CK(dalloc(ctx, &ctx->d_bias, (size_t)ctx->n_ens * 3));
+    CK(dalloc(ctx, &ctx->d_w, (size_t)ctx->n_ens));
+    CK(dalloc(ctx, &ctx->d_Nd, (size_t)ctx->n_ens));
+    CK(cudaMemcpyAsync(ctx->d_gate, ctx->gate_ix.data(), ctx->nx, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_bias, ctx->bias.data(), sizeof(double) * ctx->bias.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->d_w, ctx->w.data(), sizeof(double) * ctx->n_ens, cudaMemcpyHostToDevice, ctx->st));
+    std::vector<double> Nd(ctx->n_ens);
+    for (int e = 0; e < ctx->n_ens; ++e) Nd[e] = ctx->cfg[e].Nd_m3 * 1e-27;
+    CK(cudaMemcpyAsync(ctx->d_Nd, Nd.data(), sizeof(double) * ctx->n_ens, cudaMemcpyHostToDevice, ctx->st));
+    PoisGeo G = pgeo(ctx);
+    k_build_L<<<grid_for(n, 128), 128, 0, ctx->st>>>(ctx->Lmat, ctx->nx, ctx->ny, ctx->nz, G.ax, G.ay, G.az, ctx->d_gate);
+    CK(cudaMemcpyAsync(ctx->Ginv, ctx->Lmat, sizeof(double) * nn, cudaMemcpyDeviceToDevice, ctx->st));
+    dim3 blk(32, 8), grd(grid_for(n, 32), grid_for(n, 8));
+    double *A = ctx->Ginv, *B = ctx->rhs;  // B: temporary (rhs too small) -> use a scratch n*n
+    double* scratch = nullptr;
+    CK(cudaMalloc(&scratch, sizeof(double) * nn));
+    B = scratch;
+    for (int k = 0; k < n; ++k) {
+        k_gj<<<grd, blk, 0, ctx->st>>>(A, B, n, k);
+        std::swap(A, B);
+    }
+    ctx->launches += 1 + n;
+    if (A != ctx->Ginv) CK(cudaMemcpyAsync(ctx->Ginv, A, sizeof(double) * nn, cudaMemcpyDeviceToDevice, ctx->st));
+    k_to_f32<<<grid_for((int64_t)nn, 256), 256, 0, ctx->st>>>(ctx->Ginv, ctx->G32, (int64_t)nn);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->st));
+    cudaFree(scratch);
+    return EMC_OK;
+}
+
+// rhs from the subcell counts -> kPoissonSweeps refinement sweeps -> field
+template <typename Real>
+emc_status poisson_update(emc_ctx* ctx)
+{
+    const int n = ctx->ncell, E = ctx->n_ens;
+    const int64_t tot = (int64_t)E * n;
+    PoisGeo G = pgeo(ctx);
+    const double Vcell = ctx->dx * ctx->dy * ctx->dz;
+    k_rhs<<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->charge, nullptr, ctx->d_w, ctx->d_Nd, Vcell,
+                                                   kE2Eps0 / ctx->cfg[0].eps_s, ctx->d_bias, ctx->rhs);
+    for (int s = 0; s < kPoissonSweeps; ++s) {
+        k_resid<<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->rhs, ctx->phi, ctx->r32);
+        dim3 grd(grid_for(n, 8), grid_for(E, 8));
+        k_sweep<<<grd, 256, 0, ctx->st>>>(ctx->G32, ctx->r32, ctx->phi, n, E);
+    }
+    k_field<Real><<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->phi, ctx->dx, ctx->dy, ctx->dz, ctx->Efield,
+                                                           static_cast<Real*>(ctx->acc_cell));
+    ctx->launches += 2 + 2 * kPoissonSweeps;
+    CK(cudaGetLastError());
+    return EMC_OK;
+}
+
+void fill_params(emc_ctx* ctx)
+{
+    DevParams& P = ctx->P;
+    P.kx = ctx->kx; P.ky = ctx->ky; P.kz = ctx->kz;
+    P.x = ctx->x; P.y = ctx->y; P.z = ctx->z; P.tr = ctx->tr;
+    P.tag = ctx->tag; P.ctr = ctx->ctr; P.id = ctx->id;
+    P.n_slots = ctx->n_slots;
+    P.n_ens = ctx->n_ens;
+    P.ens_off = ctx->d_off; P.ens_cap = ctx->d_cap; P.ens_n0 = ctx->d_n0;
+    P.seed = ctx->d_seed; P.tabset = ctx->d_tabset;
+    P.acc_bulk = ctx->acc_bulk; P.acc_cell = ctx->acc_cell;
+    P.fmag_cell = nullptr;
+    P.n_target = ctx->d_target;
+    P.slot_of_id = ctx->slot_of_id; P.dead_bits = ctx->dead_bits; P.bits_off = ctx->d_bits_off;
+    P.table = ctx->table; P.phys = ctx->phys;
+    P.n_tab = ctx->n_tab; P.nb = ctx->nb;
+    P.inv_dE = 1.0 / ctx->dE;
+    P.nx = ctx->nx; P.ny = ctx->ny; P.nz = ctx->nz; P.ncell = ctx->ncell;
+    P.Lx = ctx->Lx; P.Ly = ctx->Ly; P.Lz = ctx->Lz;
+    P.dx = ctx->dx; P.dy = ctx->dy; P.dz = ctx->dz;
+    P.p_spec = ctx->cfg[0].p_specular;
+    P.dt = ctx->dt_fs;
+    P.events = ctx->events; P.cnt = ctx->cnt; P.sums = ctx->sums; P.heat = ctx->heat; P.charge = ctx->charge;
+    P.err = ctx->d_err;
+    const size_t row = (size_t)NV * NM * (ctx->prec == EMC_FP64 ? 8 : 4);
+    int nbs = (ctx->n_tab == 1) ? (int)std::min<size_t>((size_t)ctx->nb, kSmemTableBudget / row) : 0;
+    P.nb_smem = nbs;
+}
+
+emc_status check_err(emc_ctx* ctx)
+{
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device error word 0x%x (1: flight loop bound, 2: NaN energy, 4: init draws)", h);
+        return fail(ctx, EMC_EOVERFLOW, buf);
+    }
+    return EMC_OK;
+}
+
+template <typename Real>
+emc_status init_impl(emc_ctx* ctx)
+{
+    emc_status s;
+    if ((s = build_tables_and_phys<Real>(ctx)) != EMC_OK) return s;
+    if ((s = alloc_particles<Real>(ctx)) != EMC_OK) return s;
+    fill_params(ctx);
+    CK(flight_set_smem<Real>(flight_smem_bytes<Real>(ctx->P.nb_smem)));
+    launch_init<Real>(ctx->P, ctx->geom == EMC_GEOM_NANOWIRE, ctx->st);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    if (ctx->geom == EMC_GEOM_NANOWIRE) {
+        if ((s = poisson_setup(ctx)) != EMC_OK) return s;
+        // initial charge count and field
+        CK(cudaMemsetAsync(ctx->charge, 0, sizeof(int) * (size_t)ctx->n_ens * ctx->ncell, ctx->st));
+        launch_flight<Real>(ctx->P, true, 0, 1, ctx->block, ctx->st);
+        ctx->launches += 1;
+        if ((s = poisson_update<Real>(ctx)) != EMC_OK) return s;
+    }
+    CK(cudaGetLastError());
+    return check_err(ctx);
+}
+
+template <typename Real>
+emc_status step_impl(emc_ctx* ctx, int32_t n)
+{
+    const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
+    while (n > 0) {
+        int chunk;
+        bool boundary = false;
+        if (nw) {
+            const int into = int(ctx->steps_done % ctx->K);
+            chunk = std::min(n, ctx->K - into);
+            boundary = (into + chunk == ctx->K);
+            if (boundary)
+                CK(cudaMemsetAsync(ctx->charge, 0, sizeof(int) * (size_t)ctx->n_ens * ctx->ncell, ctx->st));
+        } else {
+            chunk = std::min(n, ctx->spl);
+        }
+        launch_flight<Real>(ctx->P, nw, chunk, boundary ? 1 : 0, ctx->block, ctx->st);
+        ctx->launches += 1;
+        if (boundary) {
+            launch_inject<Real>(ctx->P, ctx->st);
+            ctx->launches += 1;
+            emc_status s = poisson_update<Real>(ctx);
+            if (s != EMC_OK) return s;
+        }
+        CK(cudaGetLastError());
+        ctx->steps_done += chunk;
+        n -= chunk;
+    }
+    return EMC_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, emc_ctx** out)
+{
+    if (!out) return EMC_EINVAL;
+    *out = nullptr;
+    emc_ctx* ctx = new (std::nothrow) emc_ctx();
+    if (!ctx) return EMC_ENOMEM;
+    emc_status s = validate(cfgs, n_ens, ctx);
+    if (s != EMC_OK) {
+        *out = ctx;  // keep the message readable through emc_last_error
+        return s;
+    }
+    ctx->st = static_cast<cudaStream_t>(stream);
+    ctx->cfg.assign(cfgs, cfgs + n_ens);
+    const emc_config& c0 = cfgs[0];
+    ctx->n_ens = n_ens;
+    ctx->prec = c0.precision;
+    ctx->geom = c0.geometry;
+    ctx->nb = c0.n_bins;
+    ctx->dE = c0.dE_eV;
+    ctx->dt_fs = c0.dt_s * 1e15;
+    ctx->block = c0.block_size ? c0.block_size : 256;
+    ctx->spl = c0.steps_per_launch > 0 ? c0.steps_per_launch : 50;
+    ctx->K = c0.steps_per_poisson > 0 ? c0.steps_per_poisson : 10;
+    ctx->sort_period = c0.sort_period;
+    if (ctx->geom == EMC_GEOM_NANOWIRE) {
+        ctx->nx = c0.nx; ctx->ny = c0.ny; ctx->nz = c0.nz;
+        ctx->Lx = c0.Lx * 1e9; ctx->Ly = c0.Ly * 1e9; ctx->Lz = c0.Lz * 1e9;
+        ctx->dx = ctx->Lx / c0.nx; ctx->dy = ctx->Ly / c0.ny; ctx->dz = ctx->Lz / c0.nz;
+        ctx->gate_ix.resize(c0.nx);
+        for (int i = 0; i < c0.nx; ++i) {
+            const double xc = (i + 0.5) * c0.Lx / c0.nx;
+            ctx->gate_ix[i] = (c0.gate_on && xc >= c0.gate_x0 && xc <= c0.gate_x1) ? 1 : 0;
+        }
+    }
+    ctx->ncell = ctx->nx * ctx->ny * ctx->nz;
+    // slots, table sets
+    ctx->off.resize(n_ens);
+    ctx->cap.resize(n_ens);
+    ctx->n0.resize(n_ens);
+    ctx->tabset.resize(n_ens);
+    ctx->w.resize(n_ens);
+    ctx->bias.resize((size_t)3 * n_ens);
+    std::vector<int64_t> bits_off(n_ens);
+    std::vector<uint32_t> seeds(n_ens);
+    std::vector<int32_t> target(n_ens);
+    int64_t o = 0, bo = 0;
+    for (int e = 0; e < n_ens; ++e) {
+        const emc_config& c = cfgs[e];
+        ctx->off[e] = o;
+        ctx->cap[e] = std::max<int64_t>(c.capacity, c.n_particles);
+        ctx->n0[e] = c.n_particles;
+        o += ctx->cap[e];
+        bits_off[e] = bo;
+        bo += (ctx->cap[e] + 31) / 32;
+        seeds[e] = c.seed;
+        int ts = -1;
+        for (int f = 0; f < e && ts < 0; ++f)
+            if (same_table(cfgs[f], c)) ts = ctx->tabset[f];
+        if (ts < 0) {
+            ts = ctx->n_tab++;
+            ctx->rc.push_back(make_rc(c));
+        }
+        ctx->tabset[e] = ts;
+        const double V = c.Lx * c.Ly * c.Lz;
+        ctx->w[e] = (ctx->geom == EMC_GEOM_NANOWIRE && c.n_particles > 0) ? c.Nd_m3 * V / (double)c.n_particles : 1.0;
+        const double Vcell = V / ctx->ncell;
+        target[e] = (ctx->geom == EMC_GEOM_NANOWIRE) ? (int32_t)std::llround(c.Nd_m3 * Vcell / ctx->w[e]) : 0;
+        ctx->bias[3 * e] = c.Vs;
+        ctx->bias[3 * e + 1] = c.Vd;
+        ctx->bias[3 * e + 2] = c.Vg;
+    }
+    ctx->n_slots = o;
+    *out = ctx;
+#define CKI(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(ctx, EMC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+    const size_t n = (size_t)ctx->n_slots;
+    CKI(dalloc(ctx, &ctx->tag, n));
+    CKI(dalloc(ctx, &ctx->id, n));
+    CKI(dalloc(ctx, &ctx->slot_of_id, n));
+    CKI(dalloc(ctx, &ctx->ctr, n));
+    CKI(dalloc(ctx, &ctx->dead_bits, (size_t)bo));
+    CKI(dalloc(ctx, &ctx->d_off, n_ens));
+    CKI(dalloc(ctx, &ctx->d_cap, n_ens));
+    CKI(dalloc(ctx, &ctx->d_n0, n_ens));
+    CKI(dalloc(ctx, &ctx->d_bits_off, n_ens));
+    CKI(dalloc(ctx, &ctx->d_seed, n_ens));
+    CKI(dalloc(ctx, &ctx->d_tabset, n_ens));
+    CKI(dalloc(ctx, &ctx->d_target, n_ens));
+    CKI(dalloc(ctx, &ctx->events, (size_t)n_ens * NV * NM));
+    CKI(dalloc(ctx, &ctx->cnt, (size_t)n_ens * NCNT));
+    CKI(dalloc(ctx, &ctx->sums, (size_t)n_ens * NSUM));
+    CKI(dalloc(ctx, &ctx->heat, (size_t)n_ens * ctx->ncell * 2));
+    CKI(dalloc(ctx, &ctx->charge, (size_t)n_ens * ctx->ncell));
+    CKI(dalloc(ctx, &ctx->d_err, 1));
+    auto up = [&](void* d, const void* h, size_t b) {
+        return cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, ctx->st);
+    };
+    CKI(up(ctx->d_off, ctx->off.data(), 8 * n_ens));
+    CKI(up(ctx->d_cap, ctx->cap.data(), 8 * n_ens));
+    CKI(up(ctx->d_n0, ctx->n0.data(), 8 * n_ens));
+    CKI(up(ctx->d_bits_off, bits_off.data(), 8 * n_ens));
+    CKI(up(ctx->d_seed, seeds.data(), 4 * n_ens));
+    CKI(up(ctx->d_tabset, ctx->tabset.data(), 4 * n_ens));
+    CKI(up(ctx->d_target, target.data(), 4 * n_ens));
+#undef CKI
+    if (ctx->prec == EMC_FP64) return init_impl<double>(ctx);
+    return init_impl<float>(ctx);
+}
+
+emc_status emc_init(const emc_config* cfg, void* stream, emc_ctx** out)
+{
+    return emc_batch_init(cfg, 1, stream, out);
+}
+
+emc_status emc_step(emc_ctx* ctx, int32_t n_steps)
+{
+    if (!ctx) return EMC_EINVAL;
+    if (n_steps < 0) return fail(ctx, EMC_EINVAL, "n_steps < 0");
+    if (n_steps == 0) return EMC_OK;
+    emc_status s = ctx->prec == EMC_FP64 ? step_impl<double>(ctx, n_steps) : step_impl<float>(ctx, n_steps);
+    if (s != EMC_OK) return s;
+    return EMC_OK;
+}
+
+emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_t dst_is_device, int32_t reset)
+{
+    if (!ctx || !dst) return EMC_EINVAL;
+    const int E = ctx->n_ens, C = ctx->ncell;
+    size_t need = 0;
+    switch (kind) {
+    case EMC_TALLY_OBS: need = sizeof(emc_obs) * E; break;
+    case EMC_TALLY_EVENTS: need = 8ull * E * NV * NM; break;
+    case EMC_TALLY_HEAT: need = 8ull * E * C * 2; break;
+    case EMC_TALLY_CHARGE: need = 8ull * E * C; break;
+    case EMC_TALLY_CROSSINGS: need = 8ull * E * 4; break;
+    case EMC_TALLY_PHI: need = 8ull * E * C; break;
+    case EMC_TALLY_FIELD: need = 8ull * E * C * 3; break;
+    case EMC_TALLY_HEAT_J: need = 8ull * E * C; break;
+    default: return fail(ctx, EMC_EINVAL, "unknown tally kind");
+    }
+    if (bytes < need) return fail(ctx, EMC_EINVAL, "destination too small");
+    emc_status s = check_err(ctx);
+    if (s != EMC_OK) return s;
+    std::vector<unsigned char> host(need);
+    const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
+    if (kind == EMC_TALLY_OBS || kind == EMC_TALLY_CROSSINGS || kind == EMC_TALLY_CHARGE) {
+        std::vector<unsigned long long> cnt((size_t)E * NCNT);
+        std::vector<double> sums((size_t)E * NSUM);
+        CK(cudaMemcpyAsync(cnt.data(), ctx->cnt, 8 * cnt.size(), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(sums.data(), ctx->sums, 8 * sums.size(), cudaMemcpyDeviceToHost, ctx->st));
+        std::vector<unsigned long long> alive(E, 0);
+        if (kind == EMC_TALLY_OBS || (kind == EMC_TALLY_CHARGE && !nw)) {
+            unsigned long long* d_alive = nullptr;
+            CK(cudaMallocAsync(&d_alive, 8 * E, ctx->st));
+            CK(cudaMemsetAsync(d_alive, 0, 8 * E, ctx->st));
+            if (ctx->n_slots > 0) {
+                k_count_alive<<<grid_for(ctx->n_slots, 256), 256, 0, ctx->st>>>(ctx->tag, ctx->n_slots, d_alive);
+                ctx->launches += 1;
+            }
+            CK(cudaMemcpyAsync(alive.data(), d_alive, 8 * E, cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaFreeAsync(d_alive, ctx->st));
+        }
+        std::vector<int> ch;
+        if (kind == EMC_TALLY_CHARGE && nw) {
+            ch.resize((size_t)E * C);
+            CK(cudaMemcpyAsync(ch.data(), ctx->charge, 4 * ch.size(), cudaMemcpyDeviceToHost, ctx->st));
+        }
+        CK(cudaStreamSynchronize(ctx->st));
+        if (kind == EMC_TALLY_OBS) {
+            emc_obs* o = reinterpret_cast<emc_obs*>(host.data());
+            for (int e = 0; e < E; ++e) {
+                const unsigned long long* c = &cnt[(size_t)e * NCNT];
+                const double* sm = &sums[(size_t)e * NSUM];
+                emc_obs& q = o[e];
+                for (int i = 0; i < 3; ++i) q.sum_v[i] = sm[SUM_VX + i] * 1e6;
+                q.sum_E = sm[SUM_E] * kQ;
+                q.sum_Etot = sm[SUM_ETOT] * kQ;
+                q.n_samples = (int64_t)c[CNT_SAMPLES];
+                for (int i = 0; i < 3; ++i) {
+                    q.valley_steps[i] = (int64_t)c[CNT_V0 + i];
+                    q.self_events[i] = (int64_t)c[CNT_SELF0 + i] + (i == 0 ? 0 : 0);
+                }
+                q.overflow = (int64_t)c[CNT_OVERFLOW];
+                q.steps_done = ctx->steps_done;
+                q.n_alive = (int64_t)alive[e];
+                q.inject_starved = (int64_t)c[CNT_STARVED];
+            }
+        } else if (kind == EMC_TALLY_CROSSINGS) {
+            int64_t* o = reinterpret_cast<int64_t*>(host.data());
+            for (int e = 0; e < E; ++e) {
+                o[4 * e + 0] = (int64_t)cnt[(size_t)e * NCNT + CNT_SRC_OUT];
+                o[4 * e + 1] = (int64_t)cnt[(size_t)e * NCNT + CNT_DRN_OUT];
+                o[4 * e + 2] = (int64_t)cnt[(size_t)e * NCNT + CNT_SRC_IN];
+                o[4 * e + 3] = (int64_t)cnt[(size_t)e * NCNT + CNT_DRN_IN];
+            }
+        } else {
+            int64_t* o = reinterpret_cast<int64_t*>(host.data());
+            for (int e = 0; e < E; ++e)
+                for (int c = 0; c < C; ++c) o[(size_t)e * C + c] = nw ? ch[(size_t)e * C + c] : (int64_t)alive[e];
+        }
+    } else if (kind == EMC_TALLY_EVENTS) {
+        CK(cudaMemcpyAsync(host.data(), ctx->events, need, cudaMemcpyDeviceToHost, ctx->st));
+    } else if (kind == EMC_TALLY_HEAT) {
+        CK(cudaMemcpyAsync(host.data(), ctx->heat, need, cudaMemcpyDeviceToHost, ctx->st));
+    } else if (kind == EMC_TALLY_PHI || kind == EMC_TALLY_FIELD) {
+        if (!nw) {
+            std::memset(host.data(), 0, need);
+            if (kind == EMC_TALLY_FIELD) {
+                double* o = reinterpret_cast<double*>(host.data());
+                for (int e = 0; e < E; ++e)
+                    for (int i = 0; i < 3; ++i) o[3 * e + i] = ctx->cfg[e].field_V_m[i];
+            }
+        } else {
+            CK(cudaMemcpyAsync(host.data(), kind == EMC_TALLY_PHI ? ctx->phi : ctx->Efield, need,
+                               cudaMemcpyDeviceToHost, ctx->st));
+        }
+    } else if (kind == EMC_TALLY_HEAT_J) {
+        std::vector<long long> h((size_t)E * C * 2);
+        CK(cudaMemcpyAsync(h.data(), ctx->heat, 8 * h.size(), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        double* o = reinterpret_cast<double*>(host.data());
+        for (int e = 0; e < E; ++e)
+            for (int c = 0; c < C; ++c) {
+                const long long* hc = &h[((size_t)e * C + c) * 2];
+                o[(size_t)e * C + c] =
+                    ((double)hc[0] * ctx->cfg[e].hw_lo_eV + (double)hc[1] * ctx->cfg[e].hw_iv_eV) * kQ * ctx->w[e];
+            }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    if (dst_is_device)
+        CK(cudaMemcpyAsync(dst, host.data(), need, cudaMemcpyHostToDevice, ctx->st));
+    else
+        std::memcpy(dst, host.data(), need);
+    if (reset) {
+        CK(cudaMemsetAsync(ctx->events, 0, 8ull * E * NV * NM, ctx->st));
+        CK(cudaMemsetAsync(ctx->cnt, 0, 8ull * E * NCNT, ctx->st));
+        CK(cudaMemsetAsync(ctx->sums, 0, 8ull * E * NSUM, ctx->st));
+        CK(cudaMemsetAsync(ctx->heat, 0, 8ull * E * C * 2, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const double* bc_volts, double* phi_out)
+{
+    if (!ctx || !bc_volts) return EMC_EINVAL;
+    if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "poisson_solve needs the nanowire geometry");
+    const int n = ctx->ncell;
+    double *rho = nullptr, *rhs = nullptr, *phi = nullptr, *bias = nullptr;
+    float* r32 = nullptr;
+    CK(cudaMallocAsync(&rho, 8 * n, ctx->st));
+    CK(cudaMallocAsync(&rhs, 8 * n, ctx->st));
+    CK(cudaMallocAsync(&phi, 8 * n, ctx->st));
+    CK(cudaMallocAsync(&bias, 8 * 3, ctx->st));
+    CK(cudaMallocAsync(&r32, 4 * n, ctx->st));
+    CK(cudaMemsetAsync(phi, 0, 8 * n, ctx->st));
+    CK(cudaMemcpyAsync(bias, bc_volts, 24, cudaMemcpyHostToDevice, ctx->st));
+    PoisGeo G = pgeo(ctx);
+    const double Vcell = ctx->dx * ctx->dy * ctx->dz;
+    if (charge_or_null) {
+        CK(cudaMemcpyAsync(rho, charge_or_null, 8 * n, cudaMemcpyHostToDevice, ctx->st));
+        k_rhs<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, nullptr, rho, ctx->d_w, ctx->d_Nd, Vcell,
+                                                     kE2Eps0 / ctx->cfg[0].eps_s, bias, rhs);
+    } else {
+        k_rhs<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, ctx->charge, nullptr, ctx->d_w, ctx->d_Nd, Vcell,
+                                                     kE2Eps0 / ctx->cfg[0].eps_s, bias, rhs);
+    }
+    for (int s = 0; s < kPoissonSweeps + 1; ++s) {
+        k_resid<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, rhs, phi, r32);
+        k_sweep<<<dim3(grid_for(n, 8), 1), 256, 0, ctx->st>>>(ctx->G32, r32, phi, n, 1);
+    }
+    ctx->launches += 1 + 2 * (kPoissonSweeps + 1);
+    CK(cudaGetLastError());
+    if (phi_out) CK(cudaMemcpyAsync(phi_out, phi, 8 * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaFreeAsync(rho, ctx->st));
+    CK(cudaFreeAsync(rhs, ctx->st));
+    CK(cudaFreeAsync(phi, ctx->st));
+    CK(cudaFreeAsync(bias, ctx->st));
+    CK(cudaFreeAsync(r32, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg)
+{
+    if (!ctx || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
+    if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias needs the nanowire geometry");
+    ctx->bias[3 * ens] = Vs;
+    ctx->bias[3 * ens + 1] = Vd;
+    ctx->bias[3 * ens + 2] = Vg;
+    CK(cudaMemcpyAsync(ctx->d_bias + 3 * ens, &ctx->bias[3 * ens], 24, cudaMemcpyHostToDevice, ctx->st));
+    emc_status s = ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
+    if (s != EMC_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status emc_debug_philox(emc_ctx* ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n)
+{
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !key || !out))) return EMC_EINVAL;
+    if (n == 0) return EMC_OK;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    CK(cudaMallocAsync(&dc, 16ull * n, ctx->st));
+    CK(cudaMallocAsync(&dk, 8ull * n, ctx->st));
+    CK(cudaMallocAsync(&dout, 16ull * n, ctx->st));
+    CK(cudaMemcpyAsync(dc, ctr, 16ull * n, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(dk, key, 8ull * n, cudaMemcpyHostToDevice, ctx->st));
+    k_debug_philox<<<grid_for(n, 128), 128, 0, ctx->st>>>(dc, dk, dout, n);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, dout, 16ull * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaFreeAsync(dc, ctx->st));
+    CK(cudaFreeAsync(dk, ctx->st));
+    CK(cudaFreeAsync(dout, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status emc_debug_particles(emc_ctx* ctx, double* k, double* r, double* tr, int32_t* valley, int32_t* ens,
+                               uint32_t* idp, uint64_t* ctrp)
+{
+    if (!ctx) return EMC_EINVAL;
+    const size_t n = (size_t)ctx->n_slots;
+    const bool f64 = ctx->prec == EMC_FP64, nw = ctx->geom == EMC_GEOM_NANOWIRE;
+    const size_t es = f64 ? 8 : 4;
+    std::vector<unsigned char> b[7];
+    void* src[7] = {ctx->kx, ctx->ky, ctx->kz, ctx->x, ctx->y, ctx->z, ctx->tr};
+    for (int i = 0; i < 7; ++i) {
+        b[i].assign(n * es, 0);
+        if (src[i] && n) CK(cudaMemcpyAsync(b[i].data(), src[i], n * es, cudaMemcpyDeviceToHost, ctx->st));
+    }
+    std::vector<uint32_t> tg(n), idv(n);
+    std::vector<uint64_t> cv(n);
+    if (n) {
+        CK(cudaMemcpyAsync(tg.data(), ctx->tag, 4 * n, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(idv.data(), ctx->id, 4 * n, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(cv.data(), ctx->ctr, 8 * n, cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    auto get = [&](int a, size_t i) -> double {
+        return f64 ? reinterpret_cast<const double*>(b[a].data())[i] : (double)reinterpret_cast<const float*>(b[a].data())[i];
+    };
+    for (size_t i = 0; i < n; ++i) {
+        if (k)
+            for (int a = 0; a < 3; ++a) k[3 * i + a] = get(a, i) * 1e9;
+        if (r)
+            for (int a = 0; a < 3; ++a) r[3 * i + a] = nw ? get(3 + a, i) * 1e-9 : 0.0;
+        if (tr) tr[i] = get(6, i) * 1e-15;
+        if (valley) valley[i] = (tg[i] & 0xFFu) == DEAD ? -1 : (int32_t)(tg[i] & 0xFFu);
+        if (ens) ens[i] = (int32_t)(tg[i] >> 8);
+        if (idp) idp[i] = idv[i];
+        if (ctrp) ctrp[i] = cv[i];
+    }
+    return EMC_OK;
+}
+
+emc_status emc_debug_tables(emc_ctx* ctx, int32_t ens, double* table, double* gamma0)
+{
+    if (!ctx || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
+    const int ts = ctx->tabset[ens];
+    const size_t per = (size_t)NV * ctx->nb * NM;
+    if (table) CK(cudaMemcpyAsync(table, ctx->tab64 + ts * per, 8 * per, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (gamma0)
+        for (int v = 0; v < NV; ++v) gamma0[v] = ctx->g0_host[(size_t)ts * NV + v] * 1e15;
+    return EMC_OK;
+}
+
+emc_status emc_shape(const emc_ctx* ctx, int32_t* n_ens, int64_t* capacity, int32_t* n_cell)
+{
+    if (!ctx) return EMC_EINVAL;
+    if (n_ens) *n_ens = ctx->n_ens;
+    if (capacity) *capacity = ctx->n_slots;
+    if (n_cell) *n_cell = ctx->ncell;
+    return EMC_OK;
+}
+
+int64_t emc_launch_count(const emc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* emc_last_error(const emc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void emc_destroy(emc_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->st || true) cudaStreamSynchronize(ctx->st);
+    for (void* p : ctx->allocs) cudaFree(p);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,10 @@
+// double (parity build) instantiations of the particle kernels
+#include "kernels.cuh"
+
+namespace emc {
+template void launch_flight<double>(const DevParams&, bool, int, int, int, cudaStream_t);
+template void launch_init<double>(const DevParams&, bool, cudaStream_t);
+template void launch_inject<double>(const DevParams&, cudaStream_t);
+template cudaError_t flight_set_smem<double>(size_t);
+template size_t flight_smem_bytes<double>(int);
+}  // namespace emc

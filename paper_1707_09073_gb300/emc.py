@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libemc (include/emc.h).
+
+Argument marshalling only: every step of the Monte Carlo runs in the CUDA
+kernels of ``libemc.so``.  The library must have been built (``build.build()``)
+and a CUDA device must be present; there is no CPU fallback, and a missing
+library raises at import of the context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libemc.so")
+
+NV, NM = 3, 10
+GEOM_BULK, GEOM_NANOWIRE = 0, 1
+FP32, FP64 = 0, 1
+TALLY_OBS, TALLY_EVENTS, TALLY_HEAT, TALLY_CHARGE = 0, 1, 2, 3
+TALLY_CROSSINGS, TALLY_PHI, TALLY_FIELD, TALLY_HEAT_J = 4, 5, 6, 7
+STATUS = {0: "EMC_OK", 1: "EMC_EINVAL", 2: "EMC_ENOMEM", 3: "EMC_ECUDA", 4: "EMC_EOVERFLOW",
+          5: "EMC_ETIMEOUT", 6: "EMC_ESTATE"}
+
+
+class EmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class EmcConfig(C.Structure):
+    _fields_ = [
+        ("m_rel", C.c_double * 3), ("Ec_eV", C.c_double * 3), ("alpha_per_eV", C.c_double * 3),
+        ("eps_s", C.c_double), ("eps_inf", C.c_double), ("rho_kg_m3", C.c_double),
+        ("Da_eV", C.c_double), ("Dij_eV_per_m", C.c_double),
+        ("hw_lo_eV", C.c_double), ("hw_iv_eV", C.c_double), ("vs_m_s", C.c_double),
+        ("T_K", C.c_double), ("Nd_m3", C.c_double), ("field_V_m", C.c_double * 3),
+        ("dt_s", C.c_double), ("dE_eV", C.c_double), ("emax_init_kT", C.c_double),
+        ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+        ("gate_x0", C.c_double), ("gate_x1", C.c_double),
+        ("Vs", C.c_double), ("Vd", C.c_double), ("Vg", C.c_double), ("p_specular", C.c_double),
+        ("n_particles", C.c_int64), ("capacity", C.c_int64),
+        ("Z", C.c_int32 * 3), ("geometry", C.c_int32), ("n_bins", C.c_int32),
+        ("steps_per_poisson", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("gate_on", C.c_int32), ("seed", C.c_uint32), ("mech_mask", C.c_uint32),
+        ("precision", C.c_int32), ("sort_period", C.c_int32), ("block_size", C.c_int32),
+        ("steps_per_launch", C.c_int32),
+    ]
+
+
+class EmcObs(C.Structure):
+    _fields_ = [
+        ("sum_v", C.c_double * 3), ("sum_E", C.c_double), ("sum_Etot", C.c_double),
+        ("n_samples", C.c_int64), ("valley_steps", C.c_int64 * 3), ("self_events", C.c_int64 * 3),
+        ("overflow", C.c_int64), ("steps_done", C.c_int64), ("n_alive", C.c_int64),
+        ("inject_starved", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libemc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libemc.so not built at {LIB_PATH}; run paper_1707_09073_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64, U32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+        dp = C.POINTER(C.c_double)
+        L.emc_init.argtypes = [C.POINTER(EmcConfig), P, C.POINTER(P)]
+        L.emc_batch_init.argtypes = [C.POINTER(EmcConfig), I32, P, C.POINTER(P)]
+        L.emc_step.argtypes = [P, I32]
+        L.emc_tally.argtypes = [P, I32, P, C.c_size_t, I32, I32]
+        L.poisson_solve.argtypes = [P, dp, dp, dp]
+        L.emc_set_bias.argtypes = [P, I32, C.c_double, C.c_double, C.c_double]
+        L.emc_debug_philox.argtypes = [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32), I32]
+        L.emc_debug_particles.argtypes = [P, dp, dp, dp, C.POINTER(I32), C.POINTER(I32), C.POINTER(U32),
+                                          C.POINTER(C.c_uint64)]
+        L.emc_debug_tables.argtypes = [P, I32, dp, dp]
+        L.emc_shape.argtypes = [P, C.POINTER(I32), C.POINTER(I64), C.POINTER(I32)]
+        L.emc_launch_count.argtypes = [P]
+        L.emc_launch_count.restype = I64
+        L.emc_last_error.argtypes = [P]
+        L.emc_last_error.restype = C.c_char_p
+        L.emc_destroy.argtypes = [P]
+        for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "poisson_solve", "emc_set_bias",
+                  "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def make_config(d: dict, precision: int = FP32) -> EmcConfig:
+    """Marshal a plain configuration dict (keys of ``workloads.py``) into the C struct."""
+    c = EmcConfig()
+    c.m_rel[:] = d["m_rel"]
+    c.Ec_eV[:] = d["Ec_eV"]
+    c.alpha_per_eV[:] = d["alpha_per_eV"]
+    c.eps_s, c.eps_inf, c.rho_kg_m3 = d["eps_s"], d["eps_inf"], d["rho_kg_m3"]
+    c.Da_eV, c.Dij_eV_per_m = d["Da_eV"], d["Dij_eV_per_m"]
+    c.hw_lo_eV, c.hw_iv_eV, c.vs_m_s = d["hw_lo_eV"], d["hw_iv_eV"], d["vs_m_s"]
+    c.T_K, c.Nd_m3 = d["T"], d["Nd"]
+    c.field_V_m[:] = d["field"]
+    c.dt_s, c.dE_eV, c.emax_init_kT = d["dt"], d["dE_eV"], d["emax_init_kT"]
+    c.Lx, c.Ly, c.Lz = d["Lx"], d["Ly"], d["Lz"]
+    c.gate_x0, c.gate_x1 = d["gate_x0"], d["gate_x1"]
+    c.Vs, c.Vd, c.Vg, c.p_specular = d["Vs"], d["Vd"], d["Vg"], d["p_specular"]
+    c.n_particles, c.capacity = int(d["n_particles"]), int(d["capacity"])
+    c.Z[:] = d["Z"]
+    c.geometry, c.n_bins, c.steps_per_poisson = d["geometry"], d["n_bins"], d["steps_per_poisson"]
+    c.nx, c.ny, c.nz, c.gate_on = d["nx"], d["ny"], d["nz"], d["gate_on"]
+    c.seed = d["seed"] & 0xFFFFFFFF
+    c.mech_mask = d.get("mech_mask", 0x3FF)
+    c.precision = d.get("precision", precision)
+    c.sort_period = d.get("sort_period", 0)
+    c.block_size = d.get("block_size", 0)
+    c.steps_per_launch = d.get("steps_per_launch", 0)
+    return c
+
+
+def _p(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+class Context:
+    """One libemc context holding one or more ensembles (``emc_batch_init``).
+
+    ``stream`` is a CUDA stream handle (int) or None for the default stream;
+    with PyTorch pass ``torch.cuda.current_stream().cuda_stream``."""
+
+    def __init__(self, cfgs, precision: int = FP32, stream=None):
+        if isinstance(cfgs, dict):
+            cfgs = [cfgs]
+        self.cfgs = [dict(c) for c in cfgs]
+        arr = (EmcConfig * len(cfgs))(*[make_config(c, precision) for c in cfgs])
+        self._arr = arr
+        self.h = C.c_void_p()
+        st = lib().emc_batch_init(arr, len(cfgs), C.c_void_p(stream or 0), C.byref(self.h))
+        if st != 0:
+            msg = lib().emc_last_error(self.h).decode() if self.h else ""
+            self.close()
+            raise EmcError(st, msg)
+        ne, cap, nc = C.c_int32(), C.c_int64(), C.c_int32()
+        self._check(lib().emc_shape(self.h, C.byref(ne), C.byref(cap), C.byref(nc)))
+        self.n_ens, self.capacity, self.n_cell = ne.value, cap.value, nc.value
+
+    def _check(self, st: int):
+        if st != 0:
+            raise EmcError(st, lib().emc_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().emc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- C-ABI names ---------------------------------------------------------
+    def emc_step(self, n_steps: int):
+        self._check(lib().emc_step(self.h, int(n_steps)))
+
+    def emc_tally(self, kind: int, reset: bool = False, out=None, device: bool = False):
+        """Copy a tally (numpy array on the host, or into ``out`` when given:
+        a numpy array, or with ``device=True`` a device pointer (int) of at
+        least the tally's size in bytes)."""
+        E, Cc = self.n_ens, self.n_cell
+        spec = {
+            TALLY_OBS: (EmcObs * E, None),
+            TALLY_EVENTS: (np.uint64, (E, NV, NM)),
+            TALLY_HEAT: (np.int64, (E, Cc, 2)),
+            TALLY_CHARGE: (np.int64, (E, Cc)),
+            TALLY_CROSSINGS: (np.int64, (E, 4)),
+            TALLY_PHI: (np.float64, (E, Cc)),
+            TALLY_FIELD: (np.float64, (E, Cc, 3)),
+            TALLY_HEAT_J: (np.float64, (E, Cc)),
+        }[kind]
+        if device:
+            nbytes = C.sizeof(spec[0]) if kind == TALLY_OBS else int(np.prod(spec[1])) * np.dtype(spec[0]).itemsize
+            self._check(lib().emc_tally(self.h, kind, C.c_void_p(int(out)), nbytes, 1, int(reset)))
+            return out
+        if kind == TALLY_OBS:
+            buf = spec[0]()
+            self._check(lib().emc_tally(self.h, kind, C.byref(buf), C.sizeof(buf), 0, int(reset)))
+            return [obs_dict(buf[e]) for e in range(E)]
+        a = np.zeros(spec[1], dtype=spec[0]) if out is None else out
+        self._check(lib().emc_tally(self.h, kind, a.ctypes.data_as(C.c_void_p), a.nbytes, 0, int(reset)))
+        return a
+
+    def poisson_solve(self, charge=None, bc_volts=(0.0, 0.0, 0.0)):
+        bc = np.ascontiguousarray(bc_volts, dtype=np.float64)
+        phi = np.zeros(self.n_cell)
+        ch = None if charge is None else np.ascontiguousarray(charge, dtype=np.float64)
+        self._check(lib().poisson_solve(self.h, _p(ch) if ch is not None else None, _p(bc), _p(phi)))
+        return phi
+
+    def emc_set_bias(self, ens: int, Vs: float, Vd: float, Vg: float):
+        self._check(lib().emc_set_bias(self.h, int(ens), Vs, Vd, Vg))
+
+    def debug_philox(self, ctr, key):
+        ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+        key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+        out = np.zeros_like(ctr)
+        self._check(lib().emc_debug_philox(self.h, _p(ctr, C.c_uint32), _p(key, C.c_uint32),
+                                           _p(out, C.c_uint32), ctr.shape[0]))
+        return out
+
+    def debug_particles(self) -> dict:
+        n = self.capacity
+        k = np.zeros((n, 3)); r = np.zeros((n, 3)); tr = np.zeros(n)
+        v = np.zeros(n, np.int32); e = np.zeros(n, np.int32); i = np.zeros(n, np.uint32); c = np.zeros(n, np.uint64)
+        self._check(lib().emc_debug_particles(self.h, _p(k), _p(r), _p(tr), _p(v, C.c_int32), _p(e, C.c_int32),
+                                              _p(i, C.c_uint32), _p(c, C.c_uint64)))
+        return {"k": k, "r": r, "tr": tr, "valley": v, "ens": e, "id": i, "ctr": c}
+
+    def debug_tables(self, ens: int = 0):
+        nb = self.cfgs[ens]["n_bins"]
+        t = np.zeros((NV, nb, NM)); g = np.zeros(NV)
+        self._check(lib().emc_debug_tables(self.h, ens, _p(t), _p(g)))
+        return t, g
+
+    def launch_count(self) -> int:
+        return int(lib().emc_launch_count(self.h))
+
+
+def obs_dict(o: EmcObs) -> dict:
+    return {
+        "sum_v": np.array(o.sum_v[:]), "sum_E": o.sum_E, "sum_Etot": o.sum_Etot,
+        "n_samples": o.n_samples, "valley_steps": np.array(o.valley_steps[:], dtype=np.int64),
+        "self_events": np.array(o.self_events[:], dtype=np.int64), "overflow": o.overflow,
+        "steps_done": o.steps_done, "n_alive": o.n_alive, "inject_starved": o.inject_starved,
+    }

@@ -18,3 +18,14 @@ def oracle_mod():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def emc():
+    """The CUDA library, built in-tree for sm_103a (no fallback: a missing
+    build or device fails the test)."""
+    from paper_1707_09073_gb300 import build
+    build.build()
+    import paper_1707_09073_gb300 as m
+    m.lib()
+    return m

@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  The FP64 parity build must reproduce the oracle's integer
+tallies bit for bit over short horizons (same Philox streams, same decisions);
+floating sums agree to rounding.  The FP32 production build is compared
+statistically."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.emc_harness import gpu_tallies, oracle_heat
+
+pytestmark = pytest.mark.gpu
+
+
+def read_kat():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                v = [int(x, 16) for x in line.split()]
+                rows.append((v[:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_device_philox_known_answers(emc):
+    rows = read_kat()
+    with emc.Context(W.bulk(n_particles=1)) as ctx:
+        out = ctx.debug_philox([r[0] for r in rows], [r[1] for r in rows])
+    for o, r in zip(out, rows):
+        assert list(o) == r[2]
+
+
+def test_device_philox_matches_oracle_stream(emc, oracle_mod):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(512, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(512, 2), dtype=np.uint64).astype(np.uint32)
+    with emc.Context(W.bulk(n_particles=1)) as ctx:
+        out = ctx.debug_philox(ctr, key)
+    for i in range(0, 512, 37):
+        assert tuple(int(x) for x in out[i]) == oracle_mod.philox(tuple(int(x) for x in ctr[i]),
+                                                                  tuple(int(x) for x in key[i]))
+
+
+@pytest.mark.parametrize("cfg", [W.bulk(n_particles=1), W.bulk(n_particles=1, T=520.0, Nd_cm3=3e18),
+                                 W.nanowire(n_particles=10, nx=4, Lx=40e-9)])
+def test_rate_tables_match_oracle(emc, oracle_mod, cfg):
+    ref = oracle_mod.Sim(cfg)
+    t_ref, g_ref = ref.tables()
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        t, g = ctx.debug_tables(0)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-12)
+    np.testing.assert_allclose(t, t_ref, rtol=1e-11, atol=1e-15)
+
+
+def test_initial_state_matches_oracle(emc, oracle_mod):
+    cfg = W.nanowire(n_particles=3000, nx=10, Lx=100e-9, seed=4)
+    ref = oracle_mod.Sim(cfg).particles()
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        p = ctx.debug_particles()
+    al = ref["alive"].astype(bool)
+    assert np.array_equal(p["valley"] >= 0, al)
+    np.testing.assert_allclose(p["k"][al], ref["k"][al], rtol=1e-11, atol=1e-3)
+    np.testing.assert_allclose(p["r"][al], ref["r"][al], rtol=1e-12, atol=1e-20)
+    np.testing.assert_allclose(p["tr"][al], ref["tr"][al], rtol=1e-11)
+    assert np.array_equal(p["ctr"][al], ref["ctr"][al])
+
+
+@pytest.mark.parametrize("n,steps,spl", [(10_000, 200, 50), (1537, 60, 7)])
+def test_bulk_fp64_bit_exact(emc, oracle_mod, n, steps, spl):
+    cfg = W.bulk(n_particles=n, seed=0, steps_per_launch=spl)
+    ref = oracle_mod.Sim(cfg)
+    ref.run(steps)
+    rt = ref.tallies()
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        g = gpu_tallies(emc, ctx)
+    ob = g["obs"]
+    assert np.array_equal(g["events"], rt["events"].sum(axis=0))
+    assert np.array_equal(ob["self_events"], rt["self_events"].astype(np.int64))
+    assert np.array_equal(ob["valley_steps"], rt["valley_steps"])
+    assert ob["n_samples"] == rt["n_samples"] and ob["overflow"] == rt["overflow"]
+    np.testing.assert_allclose(ob["sum_v"], rt["sum_v"], rtol=1e-9, atol=1e-9 * np.abs(rt["sum_v"]).max())
+    assert ob["sum_E"] == pytest.approx(rt["sum_E"], rel=1e-10)
+    assert ob["sum_Etot"] == pytest.approx(rt["sum_Etot"], rel=1e-10)
+
+
+def test_nanowire_fp64_bit_exact(emc, oracle_mod):
+    cfg = W.nanowire(n_particles=6000, nx=20, Lx=200e-9, Vd=2.0, seed=7)
+    steps = 40
+    ref = oracle_mod.Sim(cfg)
+    ref.run(steps)
+    rt = ref.tallies()
+    phi_ref, E_ref = ref.phi()
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        g = gpu_tallies(emc, ctx)
+        phi = ctx.emc_tally(emc.TALLY_PHI)[0]
+        Ef = ctx.emc_tally(emc.TALLY_FIELD)[0]
+    assert np.array_equal(g["events"], rt["events"].sum(axis=0))
+    assert np.array_equal(g["heat"], oracle_heat(rt["events"]))
+    assert np.array_equal(g["crossings"], rt["crossings"])
+    assert np.array_equal(g["charge"], rt["charge"])
+    assert g["obs"]["n_alive"] == rt["n_alive"]
+    assert np.array_equal(g["obs"]["self_events"], rt["self_events"].astype(np.int64))
+    np.testing.assert_allclose(phi, phi_ref, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(Ef, E_ref, rtol=1e-7, atol=1e-3 * np.abs(E_ref).max())
+
+
+def test_poisson_solve_matches_oracle(emc, oracle_mod):
+    cfg = W.nanowire(n_particles=10)
+    rng = np.random.default_rng(3)
+    from scipy import constants as sc
+    rho = sc.e * 1e24 * rng.uniform(-1, 1, 1800)
+    want = oracle_mod.poisson(cfg, rho, tol=1e-15, maxit=50000) if False else None
+    c2 = dict(cfg); c2.update(Vs=0.0, Vd=7.0, Vg=-1.0)
+    want = oracle_mod.poisson(c2, rho, tol=1e-14)
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        got = ctx.poisson_solve(rho, (0.0, 7.0, -1.0))
+    np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-9 * np.abs(want).max())
+
+
+def test_bulk_fp32_statistics(emc, oracle_mod):
+    """Production build vs oracle at the 10,000-electron, 100 kV/cm bulk
+    workload: drift velocity, mean energy, valley fractions within 1% or 3
+    sigma of batch means (the two runs are independent samples)."""
+    cfg = W.bulk(n_particles=10_000, seed=0)
+    blocks, per = 8, 200
+    ref = oracle_mod.Sim(cfg)
+    ref.run(400)
+    with emc.Context(cfg) as ctx:
+        ctx.emc_step(400)
+        ctx.emc_tally(emc.TALLY_OBS, reset=True)
+        gv, ge, ov, oe = [], [], [], []
+        r0 = ref.tallies()
+        for b in range(blocks):
+            ctx.emc_step(per)
+            ob = ctx.emc_tally(emc.TALLY_OBS, reset=True)[0]
+            gv.append(-ob["sum_v"][2] / ob["n_samples"])
+            ge.append(ob["sum_E"] / ob["n_samples"])
+            ref.run(per)
+            r1 = ref.tallies()
+            ns = r1["n_samples"] - r0["n_samples"]
+            ov.append(-(r1["sum_v"][2] - r0["sum_v"][2]) / ns)
+            oe.append((r1["sum_E"] - r0["sum_E"]) / ns)
+            r0 = r1
+    for g, o in ((gv, ov), (ge, oe)):
+        g, o = np.array(g), np.array(o)
+        sig = np.sqrt(g.var(ddof=1) / len(g) + o.var(ddof=1) / len(o))
+        assert abs(g.mean() - o.mean()) <= max(0.01 * abs(o.mean()), 3 * sig), (g.mean(), o.mean(), sig)

@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the ensemble electron Monte Carlo (GaN half-nanowire FinFET).
+
+Workload (default): the half-nanowire drain-bias sweep -- 21 bias points
+V_ds = 0..20 V, each an ensemble of 200,000 superparticles in a 60 x 120 nm x
+1 um half wire with 3 x 6 x 100 subcells, N_d = 1e18 cm^-3, 300 K, dt = 1 fs,
+FP64 Poisson update every 10 fs -- all 21 ensembles advanced together by each
+launch.  One benchmark step = one Poisson period (10 time steps) of every bias
+point: flight/scatter/walls/tallies, contact refill, charge count, Poisson,
+field.
+
+Metric: real (non-self) electron scattering events per second, whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl emc|reference]
+
+Under torchrun (N > 1) every rank runs its own sweep with its own seeds (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "electron scatter events/sec on 1 GB300 (% roofline); surrogate vs plain MC converge time"
+UNIT = "events/s"
+STEPS_PER_POISSON = 10
+N_SM = 152
+LANES_PER_SM = 128
+# Algorithmic operation model of the flight kernel (lane operations):
+#   per real scattering: ~150 FP32 (energy, final state, angle law, rotation)
+#   + ~60 integer (one Philox4x32-10 call);
+#   per self-scattering: ~40 FP32 (energy, bin, table scan, flight time) + ~60 Philox;
+#   per particle-step: ~40 FP32 (free flight and the step sample).
+OPS_REAL, OPS_SELF, OPS_STEP = 210, 100, 40
+
+
+def sweep_configs(rank: int, n_particles: int, **tune) -> list[dict]:
+    return [W.nanowire(n_particles=n_particles, Vd=float(v), seed=1000 * rank + v, **tune) for v in range(21)]
+
+
+def workload_desc(n_particles: int) -> dict:
+    return {
+        "workload": "half-nanowire V_ds sweep: 21 bias points 0..20 V x %d superparticles, 3x6x100 subcells "
+                    "(60x120 nm x 1 um), N_d 1e18 cm^-3, 300 K, dt 1 fs, FP64 Poisson every 10 fs" % n_particles,
+        "ensembles": 21,
+        "particles_per_ensemble": n_particles,
+        "step": "one Poisson period (10 x 1 fs) of all 21 bias points",
+        "l2": "inputs larger than L2: particle state %.0f MB > 129 MB L2" % (21 * n_particles * 44 / 1e6),
+    }
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("common.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1707_09073_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic() -> float | None:
+    """DRAM bytes per flight launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "flight_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_sha") == kernel_sha():
+            return float(d["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.f = open(path, "w")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx.append(float(parts[2]))
+                    except ValueError:
+                        continue
+                    for n, v in zip(names, parts[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(n)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("EMC_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(n_particles: int, steps: int, min_seconds: float = 0.0) -> dict:
+    """The FP64 oracle as it stands, single thread, on one bias point of the
+    sweep (V_d = 10 V): real scattering events per second over `steps`
+    Poisson periods (continuing until min_seconds if given)."""
+    from oracle import oracle
+    cfg = W.nanowire(n_particles=n_particles, Vd=10.0, seed=10)
+    sim = oracle.Sim(cfg)
+    t0 = sim.tallies()
+    start = time.perf_counter()
+    done = 0
+    while done < steps or time.perf_counter() - start < min_seconds:
+        sim.run(STEPS_PER_POISSON)
+        done += 1
+    el = time.perf_counter() - start
+    t1 = sim.tallies()
+    ev = int(t1["events"].sum()) - int(t0["events"].sum())
+    return {"events": ev, "seconds": el, "periods": done, "n_particles": n_particles}
+
+
+def run_reference(args, world: int, rank: int):
+    if rank != 0:
+        return
+    n_ref = 200_000 if args.steps + args.warmup <= 400 else max(20_000, int(200_000 * 400 / (args.steps + args.warmup)))
+    from oracle import oracle
+    oracle.build()
+    cfg = W.nanowire(n_particles=n_ref, Vd=10.0, seed=10)
+    sim = oracle.Sim(cfg)
+    sim.run(STEPS_PER_POISSON * args.warmup)
+    t0 = sim.tallies()
+    start = time.perf_counter()
+    sim.run(STEPS_PER_POISSON * args.steps)
+    el = time.perf_counter() - start
+    t1 = sim.tallies()
+    ev = int(t1["events"].sum()) - int(t0["events"].sum())
+    value = ev / el
+    sample = ("FP64 oracle, single thread: 1 of the 21 bias points (V_d = 10 V), %d superparticles, "
+              "each step one Poisson period (10 x 1 fs)" % n_ref)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_desc(200_000),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU
+def run_emc(args, world: int, rank: int, local: int):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as G
+    G.build()
+    import paper_1707_09073_gb300 as emc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    n_part = args.particles
+    tune = {k: v for k, v in (("table_smem_kb", args.table_kb), ("block_size", args.block)) if v}
+    cfgs = sweep_configs(rank, n_part, **tune)
+    E = len(cfgs)
+    ctx = emc.Context(cfgs, stream=stream.cuda_stream)
+    steps = STEPS_PER_POISSON
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.emc_step(steps)
+        ctx.emc_tally(emc.TALLY_OBS, reset=True)
+        launches0 = ctx.launch_count()
+        sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        ctx.emc_profile(True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            ctx.emc_step(steps)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop()
+        ms = t_start.elapsed_time(t_end)
+        flight_ms, flight_launches = ctx.emc_profile_read()
+        ctx.emc_profile(False)
+        launches = ctx.launch_count() - launches0
+        ev = ctx.emc_tally(emc.TALLY_EVENTS)
+        obs = ctx.emc_tally(emc.TALLY_OBS, reset=True)
+    real = int(ev.sum())
+    selfe = int(sum(int(o["self_events"].sum()) for o in obs))
+    psteps = int(sum(o["n_samples"] for o in obs))
+
+    # ---- end to end through the public API with host buffers
+    bias = torch.zeros((E, 3), dtype=torch.float64).pin_memory()
+    for e, c in enumerate(cfgs):
+        bias[e, 0], bias[e, 1], bias[e, 2] = c["Vs"], c["Vd"], c["Vg"]
+    heat = np.zeros((E, ctx.n_cell, 2), dtype=np.int64)
+    cross = np.zeros((E, 4), dtype=np.int64)
+    n_e2e = max(1, min(args.steps, args.e2e_steps))
+    with torch.cuda.stream(stream):
+        ctx.emc_tally(emc.TALLY_OBS, reset=True)
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        for _ in range(n_e2e):
+            ctx.emc_set_bias_all(bias.data_ptr())
+            ctx.emc_step(steps)
+            ctx.emc_tally(emc.TALLY_OBS)
+            ctx.emc_tally(emc.TALLY_HEAT, out=heat)
+            ctx.emc_tally(emc.TALLY_CROSSINGS, out=cross)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - w0
+        ev2 = int(ctx.emc_tally(emc.TALLY_EVENTS, reset=True).sum())
+    h2d = E * 3 * 8
+    d2h = E * 128 + heat.nbytes + cross.nbytes
+
+    # ---- reduce over ranks (max time, summed events)
+    if world > 1:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        s = torch.tensor([real, selfe, psteps, ev2], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(s, op=torch.distributed.ReduceOp.SUM)
+        ms, e2e_s = float(t[0]), float(t[1])
+        real, selfe, psteps, ev2 = (int(x) for x in s.tolist())
+    ctx.close()
+    if rank != 0:
+        return
+
+    value = real / (ms * 1e-3)
+    peaks = load_peaks()
+    clk = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    # roofline of the dominant kernel (flight): lane-operation issue rate
+    per_launch_ops = (OPS_REAL * real + OPS_SELF * selfe + OPS_STEP * psteps) / max(world, 1) / max(flight_launches, 1)
+    avg_s = flight_ms * 1e-3 / max(flight_launches, 1)
+    achieved = per_launch_ops / avg_s / 1e12
+    peak_max = N_SM * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "Tops/s", "frac": achieved / peak_max,
+            "traffic": committed_traffic(), "kernel": "k_flight<float, nanowire>",
+            "peak_basis": "152 SMs x 128 lanes x %.0f MHz max SM clock (lane operations/s)" % peaks.get("sm_max_mhz", 2070.0),
+            "frac_at_sampled_clock": achieved / (N_SM * LANES_PER_SM * clk * 1e6 / 1e12),
+            "flight_share_of_step": flight_ms / ms if ms > 0 else None,
+            "op_model": {"per_real_event": OPS_REAL, "per_self_event": OPS_SELF, "per_particle_step": OPS_STEP}}
+
+    # ---- oracle on the host cores (bounded sample)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
+        oracle.build()
+        s = oracle_sample(args.cpu_particles, steps=2, min_seconds=args.cpu_seconds)
+        cpu = {"value": s["events"] / s["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle, single thread: 1 of the 21 bias points (V_d = 10 V), %d superparticles, "
+                         "%d Poisson periods (%.1f s)" % (s["n_particles"], s["periods"], s["seconds"])}
+
+    cfg = workload_desc(n_part)
+    cfg["parallelism"] = "weak: one full sweep per GPU" if world > 1 else "1 GPU"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "events_incl_self_per_s": (real + selfe) / (ms * 1e-3),
+        "particle_steps_per_s": psteps / (ms * 1e-3),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ev2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": n_e2e, "path": "emc_set_bias_all (pinned host) + emc_step + emc_tally OBS/HEAT/CROSSINGS to host"},
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
+                   "samples": clocks["samples"]},
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="emc", choices=["emc", "reference"])
+    ap.add_argument("--particles", type=int, default=200_000)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--cpu-particles", type=int, default=200_000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--table-kb", type=int, default=0, help="rate-table KiB staged in shared memory (0 = default)")
+    ap.add_argument("--block", type=int, default=0, help="flight-kernel block size (0 = default)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_emc(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

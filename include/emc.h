@@ -99,6 +99,8 @@ typedef struct emc_config {
     int32_t sort_period;    /* sort particles every this many launches (0 = never) */
     int32_t block_size;     /* flight-kernel threads per block (0 = default 256) */
     int32_t steps_per_launch; /* bulk: steps fused per flight launch (0 = default 50) */
+    int32_t table_smem_kb;  /* rate-table bytes staged in shared memory per block, KiB
+                               (0 = default 32; bins above it are read through L1/L2) */
 } emc_config;
 
 /* Per-ensemble observables accumulated over sampled particle-steps (every
@@ -171,6 +173,18 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null,
 
 /* Set the terminal voltages of ensemble ens and re-solve its field. */
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg);
+
+/* Set the terminal voltages of every ensemble from host array bias[E][3]
+ * ({Vs, Vd, Vg} per ensemble) and re-solve the fields: one host-to-device
+ * copy of 24 E bytes (asynchronous if bias is pinned). */
+emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias);
+
+/* Kernel timing: with enable = 1 every later flight-kernel launch is
+ * bracketed by CUDA events on the context stream; emc_profile_read
+ * synchronises and returns the summed flight-kernel time (ms) and launch
+ * count since the last enable, and emc_profile(ctx, 0) stops recording. */
+emc_status emc_profile(emc_ctx* ctx, int32_t enable);
+emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_launches);
 
 /* Diagnostics used by the test-suite. */
 /* Philox4x32-10 evaluated on the device for n (counter, key) pairs:

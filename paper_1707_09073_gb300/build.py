@@ -16,6 +16,9 @@ UNITS = ["emc.cu", "inst_f32.cu", "inst_f64.cu"]
 HEADERS = ["common.cuh", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# the float (production) kernels use approximate division and square root;
+# the double (parity) kernels and the host/Poisson unit stay IEEE
+UNIT_FLAGS = {"inst_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -39,7 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         src = os.path.join(CSRC, unit)
         obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
         if force or _stale(obj, [src] + deps_common):
-            cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj + ".tmp"]
+            cmd = [nvcc] + ARCH + FLAGS + UNIT_FLAGS.get(unit, []) + ["-c", src, "-o", obj + ".tmp"]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {unit}:\n{r.stdout}\n{r.stderr}")

@@ -11,7 +11,7 @@ namespace emc {
 
 constexpr int NV = 3;   // Gamma1, U, Gamma3
 constexpr int NM = 10;  // mechanisms per valley (see include/emc.h)
-constexpr int WE = 2;   // ensembles covered by a block's shared-memory tallies
+constexpr int WE = 4;   // ensembles covered by a block's shared-memory tallies
 constexpr uint32_t DEAD = 0xFFu;
 constexpr int MAX_FLIGHTS_PER_STEP = 1 << 16;
 constexpr int MAX_INIT_TRIALS = 1000;
@@ -61,9 +61,8 @@ struct DevParams {
     const int64_t* ens_n0;    // initial particles of ensemble e
     const uint32_t* seed;
     const int32_t* tabset;
-    const void* acc_bulk;     // Real[E][3]: dk/dt under the uniform field, 1/(nm fs)
-    const void* acc_cell;     // Real[E][C][3]: dk/dt per subcell
-    const double* fmag_cell;  // unused placeholder (kept for layout stability)
+    const void* acc_bulk;     // Real[E][4]: dk/dt under the uniform field, 1/(nm fs); 4th unused
+    const void* acc_cell;     // Real[E][C][4]: dk/dt per subcell and 1/(hbar |dk/dt|)
     const int32_t* n_target;  // contact-cell refill target per ensemble
     uint32_t* slot_of_id;     // [total slots] global slot of (ensemble, id)
     uint32_t* dead_bits;      // per-ensemble bitmaps of free ids
@@ -83,6 +82,7 @@ struct DevParams {
     double* sums;                 // [E][NSUM]
     long long* heat;              // [E][C][2]
     int* charge;                  // [E][C]
+    long long* alive;             // [E] live particles (never reset)
     int* err;
 };
 

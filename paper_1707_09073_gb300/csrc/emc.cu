@@ -13,19 +13,24 @@
 #include "common.cuh"
 
 namespace emc {
-template <typename Real> void launch_flight(const DevParams&, bool, int, int, int, cudaStream_t);
+template <typename Real> void launch_flight(const DevParams&, bool, int, int, int, int, cudaStream_t);
 template <typename Real> void launch_init(const DevParams&, bool, cudaStream_t);
 template <typename Real> void launch_inject(const DevParams&, cudaStream_t);
 template <typename Real> cudaError_t flight_set_smem(size_t);
-template <typename Real> size_t flight_smem_bytes(int);
+template <typename Real> size_t flight_smem_bytes(int, int);
+template <typename Real> int flight_blocks_per_sm(bool, int, size_t);
 }  // namespace emc
 
 using namespace emc;
 
 namespace {
 
-constexpr int kPoissonSweeps = 4;
-constexpr size_t kSmemTableBudget = 96 * 1024;  // bytes of rate table staged per block
+// FP64 iterative-refinement sweeps per Poisson update: the FP32 inverse
+// contracts the error by ~kappa * 2^-24 ~ 4e-4 per sweep, and the update is
+// warm-started from the previous potential, so three sweeps reach the FP64
+// residual floor; a cold start (standalone solve) takes five.
+constexpr int kPoissonSweeps = 3;
+constexpr int kSmemTableKiB = 32;  // default rate-table bytes staged per block
 constexpr int kMaxCells = 8192;                 // dense FP64 Poisson inverse limit
 
 // Golden-rule prefactors of one table set in device units (nm, fs, eV).
@@ -53,7 +58,7 @@ struct emc_ctx {
     cudaStream_t st = nullptr;
     std::vector<emc_config> cfg;
     int n_ens = 0, prec = EMC_FP32, geom = EMC_GEOM_BULK;
-    int nx = 1, ny = 1, nz = 1, ncell = 1, nb = 0, n_tab = 0, block = 256, spl = 50, K = 10;
+    int nx = 1, ny = 1, nz = 1, ncell = 1, nb = 0, n_tab = 0, block = 256, spl = 50, K = 10, grid_cap = 1;
     int sort_period = 0;
     int64_t n_slots = 0, steps_done = 0, launches = 0;
     double dt_fs = 1.0, dE = 0.002;
@@ -80,6 +85,7 @@ struct emc_ctx {
     double* sums = nullptr;
     long long* heat = nullptr;
     int* charge = nullptr;
+    long long* alive = nullptr;
     int* d_err = nullptr;
     // Poisson
     double *Lmat = nullptr, *Ginv = nullptr, *phi = nullptr, *rhs = nullptr, *Efield = nullptr, *d_bias = nullptr,
@@ -87,6 +93,10 @@ struct emc_ctx {
     float *G32 = nullptr, *r32 = nullptr;
     uint8_t* d_gate = nullptr;
     std::vector<void*> allocs;
+    // flight-kernel timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
 };
 
 namespace {
@@ -297,26 +307,44 @@ __global__ void k_resid(PoisGeo G, int n_ens, const double* rhs, const double* p
     r32[i] = float(rhs[i] - acc);
 }
 
-// phi[e] += Ginv r[e]: one warp per row, 8 ensembles per block column
-__global__ void k_sweep(const float* G32, const float* r32, double* phi, int n, int n_ens)
+// phi[e] += Ginv r[e] for 32 ensembles per grid column: a block owns 16 rows
+// (two per warp), lane = ensemble; G rows and r are staged through shared
+// memory in chunks of 64 columns.  Deterministic (no atomics).
+__global__ void __launch_bounds__(256) k_sweep(const float* G32, const float* r32, double* phi, int n, int n_ens)
 {
+    constexpr int KC = 64, RB = 16;
+    __shared__ float Gs[RB][KC];
+    __shared__ float Rs[KC][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int e0 = blockIdx.y * 8;
-    if (row >= n) return;
-    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const float* g = G32 + (size_t)row * n;
-    for (int j = lane; j < n; j += 32) {
-        const float gj = g[j];
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (e0 + c < n_ens) acc[c] += gj * r32[(size_t)(e0 + c) * n + j];
+    const int row0 = blockIdx.x * RB + 2 * warp;
+    const int e0 = blockIdx.y * 32;
+    const int ne = min(32, n_ens - e0);
+    float a[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int k0 = 0; k0 < n; k0 += KC) {
+        for (int i = threadIdx.x; i < RB * KC; i += blockDim.x) {
+            const int rr = i / KC, kk = i - rr * KC;
+            const int gr = blockIdx.x * RB + rr, gk = k0 + kk;
+            Gs[rr][kk] = (gr < n && gk < n) ? G32[(size_t)gr * n + gk] : 0.f;
+        }
+        for (int i = threadIdx.x; i < 32 * KC; i += blockDim.x) {
+            const int ee = i / KC, kk = i - ee * KC;
+            const int gk = k0 + kk;
+            Rs[kk][ee] = (ee < ne && gk < n) ? r32[(size_t)(e0 + ee) * n + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < KC; kk += 2) {
+            const float r0 = Rs[kk][lane], r1 = Rs[kk + 1][lane];
+            a[0][0] += Gs[2 * warp][kk] * r0;
+            a[0][1] += Gs[2 * warp][kk + 1] * r1;
+            a[1][0] += Gs[2 * warp + 1][kk] * r0;
+            a[1][1] += Gs[2 * warp + 1][kk + 1] * r1;
+        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        float v = acc[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        if (lane == 0 && e0 + c < n_ens) phi[(size_t)(e0 + c) * n + row] += double(v);
+    if (lane < ne) {
+        if (row0 < n) phi[(size_t)(e0 + lane) * n + row0] += double(a[0][0] + a[0][1]);
+        if (row0 + 1 < n) phi[(size_t)(e0 + lane) * n + row0 + 1] += double(a[1][0] + a[1][1]);
     }
 }
 
@@ -333,6 +361,7 @@ __global__ void k_field(PoisGeo G, int n_ens, const double* phi, double hx, doub
     const int st[3] = {G.ny * G.nz, G.nz, 1};
     const double h[3] = {hx, hy, hz};
     const double* p = phi + (size_t)e * G.n;
+    double m2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         double g;
         if (nn[a] == 1) g = 0.0;
@@ -340,17 +369,12 @@ __global__ void k_field(PoisGeo G, int n_ens, const double* phi, double hx, doub
         else if (idx[a] == nn[a] - 1) g = (p[c] - p[c - st[a]]) / h[a];
         else g = (p[c + st[a]] - p[c - st[a]]) / (2.0 * h[a]);
         const double E = -g;                        // V/nm
+        m2 += E * E;
         Efield[i * 3 + a] = E * 1e9;                // V/m
-        acc[i * 3 + a] = Real(-E / kHbarEVfs);      // dk/dt of an electron, 1/(nm fs)
+        acc[i * 4 + a] = Real(-E / kHbarEVfs);      // dk/dt of an electron, 1/(nm fs)
     }
-}
-
-__global__ void k_count_alive(const uint32_t* tag, int64_t n, unsigned long long* cnt)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = tag[i];
-    if ((t & 0xFFu) != DEAD) atomicAdd(&cnt[(size_t)(t >> 8)], 1ull);
+    // 1 / (hbar |dk/dt|) = 1 / |E| in nm/V (0 for no field)
+    acc[i * 4 + 3] = m2 > 0.0 ? Real(1.0 / sqrt(m2)) : Real(0);
 }
 
 __global__ void k_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n)
@@ -463,8 +487,9 @@ emc_status validate(const emc_config* c, int n, emc_ctx* ctx)
         } else if (b.geometry != EMC_GEOM_BULK) {
             return fail(ctx, EMC_EINVAL, "geometry");
         }
-        if (b.block_size != 0 && (b.block_size < 32 || b.block_size > 512 || b.block_size % 32))
-            return fail(ctx, EMC_EINVAL, "block_size: multiple of 32 in [32, 512]");
+        if (b.block_size != 0 && (b.block_size < 32 || b.block_size > 256 || b.block_size % 32))
+            return fail(ctx, EMC_EINVAL, "block_size: multiple of 32 in [32, 256]");
+        if (b.table_smem_kb < 0 || b.table_smem_kb > 200) return fail(ctx, EMC_EINVAL, "table_smem_kb in [0, 200]");
     }
     return EMC_OK;
 }
@@ -525,13 +550,14 @@ emc_status alloc_particles(emc_ctx* ctx)
         ctx->x = d; ctx->y = e; ctx->z = f;
     }
     Real *ab = nullptr, *ac = nullptr;
-    CK(dalloc(ctx, &ab, (size_t)ctx->n_ens * 3));
-    CK(dalloc(ctx, &ac, (size_t)ctx->n_ens * ctx->ncell * 3));
+    CK(dalloc(ctx, &ab, (size_t)ctx->n_ens * 4));
+    CK(dalloc(ctx, &ac, (size_t)ctx->n_ens * ctx->ncell * 4));
     ctx->acc_bulk = ab;
     ctx->acc_cell = ac;
-    std::vector<Real> hb((size_t)ctx->n_ens * 3);
+    // per ensemble (dk/dt of an electron, 1/(nm fs); 4th slot unused in bulk)
+    std::vector<Real> hb((size_t)ctx->n_ens * 4, Real(0));
     for (int e = 0; e < ctx->n_ens; ++e)
-        for (int i = 0; i < 3; ++i) hb[3 * e + i] = Real(-ctx->cfg[e].field_V_m[i] * 1e-9 / kHbarEVfs);
+        for (int i = 0; i < 3; ++i) hb[4 * e + i] = Real(-ctx->cfg[e].field_V_m[i] * 1e-9 / kHbarEVfs);
     CK(cudaMemcpyAsync(ab, hb.data(), sizeof(Real) * hb.size(), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
@@ -606,7 +632,7 @@ emc_status poisson_update(emc_ctx* ctx)
                                                    kE2Eps0 / ctx->cfg[0].eps_s, ctx->d_bias, ctx->rhs);
     for (int s = 0; s < kPoissonSweeps; ++s) {
         k_resid<<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->rhs, ctx->phi, ctx->r32);
-        dim3 grd(grid_for(n, 8), grid_for(E, 8));
+        dim3 grd(grid_for(n, 16), grid_for(E, 32));
         k_sweep<<<grd, 256, 0, ctx->st>>>(ctx->G32, ctx->r32, ctx->phi, n, E);
     }
     k_field<Real><<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->phi, ctx->dx, ctx->dy, ctx->dz, ctx->Efield,
@@ -627,7 +653,6 @@ void fill_params(emc_ctx* ctx)
     P.ens_off = ctx->d_off; P.ens_cap = ctx->d_cap; P.ens_n0 = ctx->d_n0;
     P.seed = ctx->d_seed; P.tabset = ctx->d_tabset;
     P.acc_bulk = ctx->acc_bulk; P.acc_cell = ctx->acc_cell;
-    P.fmag_cell = nullptr;
     P.n_target = ctx->d_target;
     P.slot_of_id = ctx->slot_of_id; P.dead_bits = ctx->dead_bits; P.bits_off = ctx->d_bits_off;
     P.table = ctx->table; P.phys = ctx->phys;
@@ -639,9 +664,11 @@ void fill_params(emc_ctx* ctx)
     P.p_spec = ctx->cfg[0].p_specular;
     P.dt = ctx->dt_fs;
     P.events = ctx->events; P.cnt = ctx->cnt; P.sums = ctx->sums; P.heat = ctx->heat; P.charge = ctx->charge;
+    P.alive = ctx->alive;
     P.err = ctx->d_err;
     const size_t row = (size_t)NV * NM * (ctx->prec == EMC_FP64 ? 8 : 4);
-    int nbs = (ctx->n_tab == 1) ? (int)std::min<size_t>((size_t)ctx->nb, kSmemTableBudget / row) : 0;
+    const int kib = ctx->cfg[0].table_smem_kb > 0 ? ctx->cfg[0].table_smem_kb : kSmemTableKiB;
+    int nbs = (ctx->n_tab == 1) ? (int)std::min<size_t>((size_t)ctx->nb, (size_t)kib * 1024 / row) : 0;
     P.nb_smem = nbs;
 }
 
@@ -665,7 +692,14 @@ emc_status init_impl(emc_ctx* ctx)
     if ((s = build_tables_and_phys<Real>(ctx)) != EMC_OK) return s;
     if ((s = alloc_particles<Real>(ctx)) != EMC_OK) return s;
     fill_params(ctx);
-    CK(flight_set_smem<Real>(flight_smem_bytes<Real>(ctx->P.nb_smem)));
+    {
+        const size_t smem = flight_smem_bytes<Real>(ctx->P.nb_smem, ctx->n_tab <= 64 ? ctx->n_tab : 0);
+        CK(flight_set_smem<Real>(smem));
+        int dev = 0, nsm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        ctx->grid_cap = nsm * flight_blocks_per_sm<Real>(ctx->geom == EMC_GEOM_NANOWIRE, ctx->block, smem);
+    }
     launch_init<Real>(ctx->P, ctx->geom == EMC_GEOM_NANOWIRE, ctx->st);
     ctx->launches += 1;
     CK(cudaGetLastError());
@@ -673,12 +707,25 @@ emc_status init_impl(emc_ctx* ctx)
         if ((s = poisson_setup(ctx)) != EMC_OK) return s;
         // initial charge count and field
         CK(cudaMemsetAsync(ctx->charge, 0, sizeof(int) * (size_t)ctx->n_ens * ctx->ncell, ctx->st));
-        launch_flight<Real>(ctx->P, true, 0, 1, ctx->block, ctx->st);
+        launch_flight<Real>(ctx->P, true, 0, 1, ctx->block, ctx->grid_cap, ctx->st);
         ctx->launches += 1;
         if ((s = poisson_update<Real>(ctx)) != EMC_OK) return s;
     }
     CK(cudaGetLastError());
     return check_err(ctx);
+}
+
+emc_status prof_pair(emc_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b)
+{
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
+    }
+    *a = ctx->ev_pool[ctx->ev_used];
+    *b = ctx->ev_pool[ctx->ev_used + 1];
+    ctx->ev_used += 2;
+    return EMC_OK;
 }
 
 template <typename Real>
@@ -697,8 +744,15 @@ emc_status step_impl(emc_ctx* ctx, int32_t n)
         } else {
             chunk = std::min(n, ctx->spl);
         }
-        launch_flight<Real>(ctx->P, nw, chunk, boundary ? 1 : 0, ctx->block, ctx->st);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ctx->prof) {
+            emc_status s = prof_pair(ctx, &e0, &e1);
+            if (s != EMC_OK) return s;
+            CK(cudaEventRecord(e0, ctx->st));
+        }
+        launch_flight<Real>(ctx->P, nw, chunk, boundary ? 1 : 0, ctx->block, ctx->grid_cap, ctx->st);
         ctx->launches += 1;
+        if (ctx->prof) CK(cudaEventRecord(e1, ctx->st));
         if (boundary) {
             launch_inject<Real>(ctx->P, ctx->st);
             ctx->launches += 1;
@@ -813,6 +867,7 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
     CKI(dalloc(ctx, &ctx->sums, (size_t)n_ens * NSUM));
     CKI(dalloc(ctx, &ctx->heat, (size_t)n_ens * ctx->ncell * 2));
     CKI(dalloc(ctx, &ctx->charge, (size_t)n_ens * ctx->ncell));
+    CKI(dalloc(ctx, &ctx->alive, n_ens));
     CKI(dalloc(ctx, &ctx->d_err, 1));
     auto up = [&](void* d, const void* h, size_t b) {
         return cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, ctx->st);
@@ -824,6 +879,7 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
     CKI(up(ctx->d_seed, seeds.data(), 4 * n_ens));
     CKI(up(ctx->d_tabset, ctx->tabset.data(), 4 * n_ens));
     CKI(up(ctx->d_target, target.data(), 4 * n_ens));
+    CKI(up(ctx->alive, ctx->n0.data(), 8 * n_ens));
 #undef CKI
     if (ctx->prec == EMC_FP64) return init_impl<double>(ctx);
     return init_impl<float>(ctx);
@@ -870,18 +926,8 @@ emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_
         std::vector<double> sums((size_t)E * NSUM);
         CK(cudaMemcpyAsync(cnt.data(), ctx->cnt, 8 * cnt.size(), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(sums.data(), ctx->sums, 8 * sums.size(), cudaMemcpyDeviceToHost, ctx->st));
-        std::vector<unsigned long long> alive(E, 0);
-        if (kind == EMC_TALLY_OBS || (kind == EMC_TALLY_CHARGE && !nw)) {
-            unsigned long long* d_alive = nullptr;
-            CK(cudaMallocAsync(&d_alive, 8 * E, ctx->st));
-            CK(cudaMemsetAsync(d_alive, 0, 8 * E, ctx->st));
-            if (ctx->n_slots > 0) {
-                k_count_alive<<<grid_for(ctx->n_slots, 256), 256, 0, ctx->st>>>(ctx->tag, ctx->n_slots, d_alive);
-                ctx->launches += 1;
-            }
-            CK(cudaMemcpyAsync(alive.data(), d_alive, 8 * E, cudaMemcpyDeviceToHost, ctx->st));
-            CK(cudaFreeAsync(d_alive, ctx->st));
-        }
+        std::vector<long long> alive(E, 0);
+        CK(cudaMemcpyAsync(alive.data(), ctx->alive, 8 * E, cudaMemcpyDeviceToHost, ctx->st));
         std::vector<int> ch;
         if (kind == EMC_TALLY_CHARGE && nw) {
             ch.resize((size_t)E * C);
@@ -989,7 +1035,7 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
     }
     for (int s = 0; s < kPoissonSweeps + 1; ++s) {
         k_resid<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, rhs, phi, r32);
-        k_sweep<<<dim3(grid_for(n, 8), 1), 256, 0, ctx->st>>>(ctx->G32, r32, phi, n, 1);
+        k_sweep<<<dim3(grid_for(n, 16), 1), 256, 0, ctx->st>>>(ctx->G32, r32, phi, n, 1);
     }
     ctx->launches += 1 + 2 * (kPoissonSweeps + 1);
     CK(cudaGetLastError());
@@ -1014,6 +1060,38 @@ emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double 
     emc_status s = ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
     if (s != EMC_OK) return s;
     CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias)
+{
+    if (!ctx || !bias) return EMC_EINVAL;
+    if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias_all needs the nanowire geometry");
+    std::memcpy(ctx->bias.data(), bias, sizeof(double) * 3 * ctx->n_ens);
+    CK(cudaMemcpyAsync(ctx->d_bias, bias, sizeof(double) * 3 * ctx->n_ens, cudaMemcpyHostToDevice, ctx->st));
+    return ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
+}
+
+emc_status emc_profile(emc_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return EMC_EINVAL;
+    ctx->prof = enable != 0;
+    if (enable) ctx->ev_used = 0;
+    return EMC_OK;
+}
+
+emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_launches)
+{
+    if (!ctx) return EMC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->st));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+        tot += ms;
+    }
+    if (flight_ms) *flight_ms = tot;
+    if (flight_launches) *flight_launches = (int64_t)(ctx->ev_used / 2);
     return EMC_OK;
 }
 
@@ -1104,7 +1182,8 @@ const char* emc_last_error(const emc_ctx* ctx) { return ctx ? ctx->err.c_str() :
 void emc_destroy(emc_ctx* ctx)
 {
     if (!ctx) return;
-    if (ctx->st || true) cudaStreamSynchronize(ctx->st);
+    cudaStreamSynchronize(ctx->st);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
 }

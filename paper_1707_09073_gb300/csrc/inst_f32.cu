@@ -1,10 +1,11 @@
-// float (production) instantiations of the particle kernels
+// float instantiations of the particle kernels (production build)
 #include "kernels.cuh"
 
 namespace emc {
-template void launch_flight<float>(const DevParams&, bool, int, int, int, cudaStream_t);
+template void launch_flight<float>(const DevParams&, bool, int, int, int, int, cudaStream_t);
 template void launch_init<float>(const DevParams&, bool, cudaStream_t);
 template void launch_inject<float>(const DevParams&, cudaStream_t);
 template cudaError_t flight_set_smem<float>(size_t);
-template size_t flight_smem_bytes<float>(int);
+template size_t flight_smem_bytes<float>(int, int);
+template int flight_blocks_per_sm<float>(bool, int, size_t);
 }  // namespace emc

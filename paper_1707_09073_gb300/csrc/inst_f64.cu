@@ -1,10 +1,11 @@
-// double (parity build) instantiations of the particle kernels
+// double instantiations of the particle kernels (parity build)
 #include "kernels.cuh"
 
 namespace emc {
-template void launch_flight<double>(const DevParams&, bool, int, int, int, cudaStream_t);
+template void launch_flight<double>(const DevParams&, bool, int, int, int, int, cudaStream_t);
 template void launch_init<double>(const DevParams&, bool, cudaStream_t);
 template void launch_inject<double>(const DevParams&, cudaStream_t);
 template cudaError_t flight_set_smem<double>(size_t);
-template size_t flight_smem_bytes<double>(int);
+template size_t flight_smem_bytes<double>(int, int);
+template int flight_blocks_per_sm<double>(bool, int, size_t);
 }  // namespace emc

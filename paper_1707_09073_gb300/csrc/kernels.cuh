@@ -15,14 +15,28 @@
 namespace emc {
 
 // ------------------------------------------------------------- math
+// The float build compiles with approximate division and square root
+// (-prec-div=false -prec-sqrt=false); logarithm and sine/cosine go to the
+// special-function unit with the argument kept in its accurate range.
 template <typename Real>
 struct Mth;
 template <>
 struct Mth<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    // -ln(u) of a uniform in (0,1) for a flight time: never negative
+    static __device__ __forceinline__ float neglog_u(float u) { return fmaxf(0.f, -__logf(u)); }
     static __device__ __forceinline__ float pow_(float b, float e) { return exp2f(e * log2f(b)); }
     static __device__ __forceinline__ void sincospi_(float x, float* s, float* c) { sincospif(x, s, c); }
+    // sin and cos of 2 pi u, u in (0,1): evaluated at 2 pi (u - 1/2) in (-pi, pi)
+    // where the hardware approximation is accurate, then negated
+    static __device__ __forceinline__ void sincos2pi_u(float u, float* s, float* c)
+    {
+        float ss, cc;
+        __sincosf(6.283185307179586f * (u - 0.5f), &ss, &cc);
+        *s = -ss;
+        *c = -cc;
+    }
     static __device__ __forceinline__ float cospi_(float x) { return cospif(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
 };
@@ -30,8 +44,10 @@ template <>
 struct Mth<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double neglog_u(double u) { return -log(u); }
     static __device__ __forceinline__ double pow_(double b, double e) { return pow(b, e); }
     static __device__ __forceinline__ void sincospi_(double x, double* s, double* c) { sincospi(x, s, c); }
+    static __device__ __forceinline__ void sincos2pi_u(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
     static __device__ __forceinline__ double cospi_(double x) { return cospi(x); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
 };
@@ -56,14 +72,25 @@ struct Acc {
         s = t;
     }
     __device__ __forceinline__ double value() const { return double(s) - double(c); }
+    __device__ __forceinline__ void clear() { s = c = 0; }
 };
 template <>
 struct Acc<double> {
     double s = 0;
     __device__ __forceinline__ void add(double x) { s += x; }
     __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ void clear() { s = 0; }
 };
 
+// Launch constants in the kernel's own precision (no conversions in the loop).
+template <typename Real>
+struct KConst {
+    Real Lx, Ly, Lz, inv_dx, inv_dy, inv_dz, p_spec, dt, inv_dE;
+    int nx, ny, nz, ncell, nb, nbs, n_tab, n_tab_s;
+    int64_t per_block;
+};
+
+// Shared-memory tallies of the ensembles [e_base, e_base + WE) of a block.
 struct BlockTally {
     unsigned int ev[WE][NV * NM];
     unsigned int cnt[WE][NCNT];
@@ -74,16 +101,19 @@ __device__ __forceinline__ void tally_cnt(BlockTally* bt, const DevParams& P, in
                                           int idx, unsigned int n)
 {
     const int w = e - e_base;
-    if (w >= 0 && w < WE)
+    if (w >= 0 && w < WE) {
         atomicAdd(&bt->cnt[w][idx], n);
-    else
+    } else {
         atomicAdd(&P.cnt[(size_t)e * NCNT + idx], (unsigned long long)n);
+        if (idx == CNT_SRC_OUT || idx == CNT_DRN_OUT)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&P.alive[e]), (unsigned long long)(-(long long)n));
+    }
 }
 
 // ------------------------------------------------------------ particle
 template <typename Real>
 struct Part {
-    Real kx, ky, kz, x, y, z, tr;
+    Real kx, ky, kz, x, y, z, tr, E;  // E: kinetic energy of k, carried along
     uint64_t ctr;
     uint32_t id, seed;
     int v, e;
@@ -97,19 +127,31 @@ struct Part {
 };
 
 template <typename Real>
-__device__ __forceinline__ int cell_of(const DevParams& P, Real x, Real y, Real z)
+__device__ __forceinline__ int cell_of(const KConst<Real>& K, Real x, Real y, Real z)
 {
-    Real fx = Mth<Real>::floor_(x / Real(P.dx));
-    Real fy = Mth<Real>::floor_(y / Real(P.dy));
-    Real fz = Mth<Real>::floor_(z / Real(P.dz));
-    int ix = fx >= Real(0) ? (fx < Real(P.nx) ? int(fx) : P.nx - 1) : 0;
-    int iy = fy >= Real(0) ? (fy < Real(P.ny) ? int(fy) : P.ny - 1) : 0;
-    int iz = fz >= Real(0) ? (fz < Real(P.nz) ? int(fz) : P.nz - 1) : 0;
-    return (ix * P.ny + iy) * P.nz + iz;
+    const Real fx = Mth<Real>::floor_(x * K.inv_dx);
+    const Real fy = Mth<Real>::floor_(y * K.inv_dy);
+    const Real fz = Mth<Real>::floor_(z * K.inv_dz);
+    const int ix = fx >= Real(0) ? (fx < Real(K.nx) ? int(fx) : K.nx - 1) : 0;
+    const int iy = fy >= Real(0) ? (fy < Real(K.ny) ? int(fy) : K.ny - 1) : 0;
+    const int iz = fz >= Real(0) ? (fz < Real(K.nz) ? int(fz) : K.nz - 1) : 0;
+    return (ix * K.ny + iy) * K.nz + iz;
 }
 
-// Kane-Maxwellian g(E) exp(-E/kT) in valley 0 by rejection: proposal
-// -kT (ln u0 + ln u1 cos^2(pi u2 / 2)) ~ Gamma(3/2, kT), accepted when
+template <typename Real>
+__device__ __forceinline__ void load4(const Real* p, Real o[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float o[4])
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* p, double o[4])
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
 // u3 h(Emax) <= h(E), h(E) = sqrt(1 + aE)(1 + 2aE), E <= Emax.
 template <typename Real>
 __device__ Real draw_maxwell(Part<Real>& q, const Phys<Real>* ph, int* err)
@@ -170,35 +212,39 @@ __device__ __forceinline__ void store(const DevParams& P, int64_t s, const Part<
     static_cast<Real*>(P.tr)[s] = q.tr;
     P.ctr[s] = q.ctr;
 }
-
 // --------------------------------------------------------- free flight
-// k advances linearly (hbar dk/dt = force); in the nanowire the position
-// moves along the force by the energy gained over the force and across it by
-// the mean of the start and end group velocities times t.
+// k advances linearly (hbar dk/dt = force = hbar a); the carried energy is
+// updated.  In the nanowire the position moves along the force by the energy
+// gained over the force (exact for any band) and across it by the mean of the
+// start and end group velocities times t.  f4 = (a_x, a_y, a_z, 1/(hbar |a|)).
 template <typename Real, bool NW>
-__device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>* ph, const Real a[3],
-                                      const Real ah[3], Real inv_hF, Real t)
+__device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>& ph, const Real f4[4], Real t)
 {
     const Real k0x = q.kx, k0y = q.ky, k0z = q.kz;
-    q.kx = k0x + a[0] * t;
-    q.ky = k0y + a[1] * t;
-    q.kz = k0z + a[2] * t;
+    q.kx = k0x + f4[0] * t;
+    q.ky = k0y + f4[1] * t;
+    q.kz = k0z + f4[2] * t;
+    const int v = q.v;
+    const Real al = ph.alpha[v];
+    const Real E0 = q.E;
+    const Real E1 = kane_E(ph.ck[v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), al);
+    q.E = E1;
     if (NW) {
-        const int v = q.v;
-        const Real ck = ph->ck[v], al = ph->alpha[v], vk = ph->vk[v];
-        const Real E0 = kane_E(ck * (k0x * k0x + k0y * k0y + k0z * k0z), al);
-        const Real E1 = kane_E(ck * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), al);
+        const Real vk = ph.vk[v];
         const Real f0 = vk / (Real(1) + Real(2) * al * E0);
         const Real f1 = vk / (Real(1) + Real(2) * al * E1);
         const Real h = Real(0.5) * t;
         Real dx = h * (f0 * k0x + f1 * q.kx);
         Real dy = h * (f0 * k0y + f1 * q.ky);
         Real dz = h * (f0 * k0z + f1 * q.kz);
-        if (inv_hF > Real(0)) {
-            const Real d = (E1 - E0) * inv_hF - (dx * ah[0] + dy * ah[1] + dz * ah[2]);
-            dx += d * ah[0];
-            dy += d * ah[1];
-            dz += d * ah[2];
+        const Real ihF = f4[3];
+        if (ihF > Real(0)) {
+            const Real s = Real(kHbarEVfs) * ihF;  // 1/|a|
+            const Real ax = f4[0] * s, ay = f4[1] * s, az = f4[2] * s;
+            const Real d = (E1 - E0) * ihF - (dx * ax + dy * ay + dz * az);
+            dx += d * ax;
+            dy += d * ay;
+            dz += d * az;
         }
         q.x += dx;
         q.y += dy;
@@ -218,7 +264,7 @@ __device__ __forceinline__ void diffuse(Part<Real>& q, int axis, Real sn, U4 r)
     const Real u1 = u01<Real>(r.b);
     const Real ca = Mth<Real>::sqrt_(u1), sa = Mth<Real>::sqrt_(Real(1) - u1);
     Real sp, cp;
-    Mth<Real>::sincospi_(Real(2) * u01<Real>(r.c), &sp, &cp);
+    Mth<Real>::sincos2pi_u(u01<Real>(r.c), &sp, &cp);
     q.kx = km * sa * cp;
     if (axis == 1) {
         q.ky = km * sn * ca;
@@ -230,12 +276,12 @@ __device__ __forceinline__ void diffuse(Part<Real>& q, int axis, Real sn, U4 r)
 }
 
 template <typename Real>
-__device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, BlockTally* bt, int e_base)
+__device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, const KConst<Real>& K, BlockTally* bt,
+                                      int e_base)
 {
-    const Real Lx = Real(P.Lx), Ly = Real(P.Ly), Lz = Real(P.Lz), ps = Real(P.p_spec);
     int out = -1;
     if (q.x < Real(0)) out = CNT_SRC_OUT;
-    else if (q.x > Lx) out = CNT_DRN_OUT;
+    else if (q.x > K.Lx) out = CNT_DRN_OUT;
     if (out >= 0) {
         tally_cnt(bt, P, q.e, e_base, out, 1u);
         atomicOr(&P.dead_bits[P.bits_off[q.e] + (q.id >> 5)], 1u << (q.id & 31u));
@@ -244,25 +290,25 @@ __device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, BlockTa
     if (q.y < Real(0)) {
         q.y = -q.y;
         q.ky = -q.ky;
-    } else if (q.y > Ly) {
-        q.y = Real(2) * Ly - q.y;
-        U4 r = q.draw();
-        if (u01<Real>(r.a) < ps) q.ky = -q.ky;
+    } else if (q.y > K.Ly) {
+        q.y = Real(2) * K.Ly - q.y;
+        const U4 r = q.draw();
+        if (u01<Real>(r.a) < K.p_spec) q.ky = -q.ky;
         else diffuse(q, 1, Real(-1), r);
     }
-    q.y = q.y < Real(0) ? Real(0) : (q.y > Ly ? Ly : q.y);
+    q.y = q.y < Real(0) ? Real(0) : (q.y > K.Ly ? K.Ly : q.y);
     if (q.z < Real(0)) {
         q.z = -q.z;
-        U4 r = q.draw();
-        if (u01<Real>(r.a) < ps) q.kz = -q.kz;
+        const U4 r = q.draw();
+        if (u01<Real>(r.a) < K.p_spec) q.kz = -q.kz;
         else diffuse(q, 2, Real(1), r);
-    } else if (q.z > Lz) {
-        q.z = Real(2) * Lz - q.z;
-        U4 r = q.draw();
-        if (u01<Real>(r.a) < ps) q.kz = -q.kz;
+    } else if (q.z > K.Lz) {
+        q.z = Real(2) * K.Lz - q.z;
+        const U4 r = q.draw();
+        if (u01<Real>(r.a) < K.p_spec) q.kz = -q.kz;
         else diffuse(q, 2, Real(-1), r);
     }
-    q.z = q.z < Real(0) ? Real(0) : (q.z > Lz ? Lz : q.z);
+    q.z = q.z < Real(0) ? Real(0) : (q.z > K.Lz ? K.Lz : q.z);
     return false;
 }
 
@@ -270,21 +316,35 @@ __device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, BlockTa
 // One Philox call per scattering: u0 picks the mechanism against the
 // cumulative table row of the current energy bin (lower bin edge; above the
 // last entry = self-scattering), u2/u3 the final direction, u1 the next
-// flight time -ln(u1)/Gamma0 of the final valley.
-template <typename Real, bool NW>
-__device__ __forceinline__ void scatter(Part<Real>& q, const DevParams& P, const Phys<Real>* ph,
-                                        const Real* tab_s, int nbs, const Real* tab_g, BlockTally* bt,
-                                        int e_base)
+// flight time -ln(u1)/Gamma0 of the final valley.  Split in two so that the
+// block can compact the real scatterings before the final-state code.
+
+// A queued scattering: the particle plus the draws of its Philox call.
+template <typename Real>
+struct QEntry {
+    Part<Real> q;
+    Real u1, u2, u3;
+    int mech;
+};
+
+// Mechanism choice.  Returns the mechanism (-1: self-scattering, whose next
+// flight time is set here).
+template <typename Real>
+__device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const KConst<Real>& K, const Phys<Real>& ph,
+                                      const Real* tab_s, int nbs, const Real* tab_g, BlockTally* bt, int e_base)
 {
+    Part<Real>& q = Q.q;
     const U4 r = q.draw();
-    const Real u0 = u01<Real>(r.a), u1 = u01<Real>(r.b), u2 = u01<Real>(r.c), u3 = u01<Real>(r.d);
+    const Real u0 = u01<Real>(r.a);
+    Q.u1 = u01<Real>(r.b);
+    Q.u2 = u01<Real>(r.c);
+    Q.u3 = u01<Real>(r.d);
     const int v = q.v;
-    const Real k2 = q.kx * q.kx + q.ky * q.ky + q.kz * q.kz;
-    const Real E = kane_E(ph->ck[v] * k2, ph->alpha[v]);
-    const Real fb = Mth<Real>::floor_(E * Real(P.inv_dE));
+    const Real E = q.E;
+    const Real fb = Mth<Real>::floor_(E * K.inv_dE);
     int b;
-    if (fb >= Real(P.nb)) {
-        b = P.nb - 1;
+    if (fb >= Real(K.nb)) {
+        b = K.nb - 1;
         tally_cnt(bt, P, q.e, e_base, CNT_OVERFLOW, 1u);
     } else if (fb >= Real(0)) {
         b = int(fb);
@@ -292,244 +352,264 @@ __device__ __forceinline__ void scatter(Part<Real>& q, const DevParams& P, const
         b = 0;
         if (!(E == E)) atomicOr(P.err, ERR_NAN);
     }
-    const Real* row = (b < nbs) ? tab_s + ((size_t)v * nbs + b) * NM
-                                : tab_g + ((size_t)v * P.nb + b) * NM;
+    const Real* row = (b < nbs) ? tab_s + ((size_t)v * nbs + b) * NM : tab_g + ((size_t)v * K.nb + b) * NM;
     int mech = -1;
     if (u0 < row[NM - 1]) {
 #pragma unroll
         for (int m = 0; m < NM; ++m)
             if (mech < 0 && u0 < row[m]) mech = m;
     }
-    int vn = v;
     if (mech >= 0) {
-        int j = v;
+        // final energy; a channel that cannot conserve energy counts as self
         Real Ep;
-        if (mech == 0 || mech == 3) {
-            Ep = E;
-        } else if (mech == 1) {
-            Ep = E + ph->hw_lo;
-        } else if (mech == 2) {
-            Ep = E - ph->hw_lo;
-        } else {
-            j = (mech - 4) >> 1;
-            Ep = E + ((mech & 1) == 0 ? ph->hw_iv : -ph->hw_iv) - (ph->Ec[j] - ph->Ec[v]);
+        if (mech == 0 || mech == 3) Ep = E;
+        else if (mech == 1) Ep = E + ph.hw_lo;
+        else if (mech == 2) Ep = E - ph.hw_lo;
+        else {
+            const int j = (mech - 4) >> 1;
+            Ep = E + ((mech & 1) == 0 ? ph.hw_iv : -ph.hw_iv) - (ph.Ec[j] - ph.Ec[v]);
         }
         if (!(Ep > Real(0))) {
             tally_cnt(bt, P, q.e, e_base, CNT_REJECT, 1u);
             mech = -1;
-        } else {
-            const Real km = Mth<Real>::sqrt_(k2);
-            const Real kp = Mth<Real>::sqrt_(Ep * (Real(1) + ph->alpha[j] * Ep) / ph->ck[j]);
-            Real ct;
-            bool rel = true;
-            if (mech == 0) {
-                // Brooks-Herring: P(cos) ~ 1 / (2k^2 (1 - cos) + beta^2)^2
-                ct = Real(1) - Real(2) * u2 / (Real(1) + Real(4) * k2 * (Real(1) - u2) / ph->beta2);
-            } else if (mech <= 2) {
-                // Froehlich: P(cos) ~ 1 / (k^2 + k'^2 - 2 k k' cos)
-                const Real d = km - kp;
-                const Real xi = Real(2) * km * kp / (d * d);
-                ct = (xi >= Real(1e-6)) ? ((Real(1) + xi) - Mth<Real>::pow_(Real(1) + Real(2) * xi, u2)) / xi
-                                        : Real(1) - Real(2) * u2;
-            } else {
-                ct = Real(1) - Real(2) * u2;  // isotropic
-                rel = false;
-            }
-            Real sp, cp;
-            Mth<Real>::sincospi_(Real(2) * u3, &sp, &cp);
-            const Real st = Mth<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
-            Real dx, dy, dz;
-            if (rel) {
-                // frame of k: branchless orthonormal basis (Duff et al., JCGT 2017)
-                Real nx = 0, ny = 0, nz = 1;
-                if (km > Real(0)) {
-                    nx = q.kx / km;
-                    ny = q.ky / km;
-                    nz = q.kz / km;
-                }
-                const Real sg = copysign(Real(1), nz);
-                const Real aa = Real(-1) / (sg + nz);
-                const Real bb = nx * ny * aa;
-                const Real e1x = Real(1) + sg * nx * nx * aa, e1y = sg * bb, e1z = -sg * nx;
-                const Real e2x = bb, e2y = sg + ny * ny * aa, e2z = -ny;
-                dx = st * cp * e1x + st * sp * e2x + ct * nx;
-                dy = st * cp * e1y + st * sp * e2y + ct * ny;
-                dz = st * cp * e1z + st * sp * e2z + ct * nz;
-            } else {
-                dx = st * cp;
-                dy = st * sp;
-                dz = ct;
-            }
-            q.kx = kp * dx;
-            q.ky = kp * dy;
-            q.kz = kp * dz;
-            vn = j;
-            const int w = q.e - e_base;
-            if (w >= 0 && w < WE)
-                atomicAdd(&bt->ev[w][v * NM + mech], 1u);
-            else
-                atomicAdd(&P.events[((size_t)q.e * NV + v) * NM + mech], 1ull);
-            if (NW && mech != 0 && mech != 3) {
-                const int c = cell_of<Real>(P, q.x, q.y, q.z);
-                // net emission: mech 1 absorbs, 2 emits; 4+2j absorbs, 5+2j emits
-                const long long d = (mech == 1) ? -1 : (mech == 2 ? 1 : ((mech & 1) ? 1 : -1));
-                atomicAdd(reinterpret_cast<unsigned long long*>(
-                              &P.heat[((size_t)q.e * P.ncell + c) * 2 + (mech <= 2 ? 0 : 1)]),
-                          (unsigned long long)d);
-            }
         }
     }
-    if (mech < 0) tally_cnt(bt, P, q.e, e_base, CNT_SELF0 + v, 1u);
-    q.v = vn;
-    q.tr = -Mth<Real>::log_(u1) * ph->inv_g0[vn];
+    if (mech < 0) {
+        tally_cnt(bt, P, q.e, e_base, CNT_SELF0 + v, 1u);
+        q.tr = Mth<Real>::neglog_u(Q.u1) * ph.inv_g0[v];
+    }
+    Q.mech = mech;
+    return mech;
 }
 
-// -------------------------------------------------------------- flight
-// One thread per particle slot; n_steps time steps fused.  Tables of a
-// single table set are staged in shared memory for bins [0, nb_smem).
+// Final state of a real scattering (mech >= 0) and the next flight time.
 template <typename Real, bool NW>
-__global__ void __launch_bounds__(512) k_flight(const DevParams P, int n_steps, int count_charge)
+__device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P, const KConst<Real>& K,
+                                            const Phys<Real>& ph, BlockTally* bt, int e_base)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int nbs = P.nb_smem;
-    Real* tab_s = reinterpret_cast<Real*>(sm);
-    size_t tbytes = ((size_t)NV * nbs * NM * sizeof(Real) + 15) & ~size_t(15);
-    BlockTally* bt = reinterpret_cast<BlockTally*>(sm + tbytes);
-    const Real* tab_all = static_cast<const Real*>(P.table);
-    for (int i = threadIdx.x; i < NV * nbs * NM; i += blockDim.x) {
-        const int v = i / (nbs * NM), rr = i - v * nbs * NM;
-        tab_s[i] = tab_all[(size_t)v * P.nb * NM + rr];
+    Part<Real>& q = Q.q;
+    const int mech = Q.mech, v = q.v;
+    const Real E = q.E, u2 = Q.u2;
+    int j = v;
+    Real Ep;
+    if (mech == 0 || mech == 3) {
+        Ep = E;
+    } else if (mech == 1) {
+        Ep = E + ph.hw_lo;
+    } else if (mech == 2) {
+        Ep = E - ph.hw_lo;
+    } else {
+        j = (mech - 4) >> 1;
+        Ep = E + ((mech & 1) == 0 ? ph.hw_iv : -ph.hw_iv) - (ph.Ec[j] - ph.Ec[v]);
     }
-    for (int i = threadIdx.x; i < (int)(sizeof(BlockTally) / 4); i += blockDim.x)
-        reinterpret_cast<unsigned int*>(bt)[i] = 0u;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int e_base = int(P.tag[(int64_t)blockIdx.x * blockDim.x] >> 8);
-    __syncthreads();
+    const Real k2 = q.kx * q.kx + q.ky * q.ky + q.kz * q.kz;
+    const Real km = Mth<Real>::sqrt_(k2);
+    const Real kp = Mth<Real>::sqrt_(Ep * (Real(1) + ph.alpha[j] * Ep) / ph.ck[j]);
+    Real ct;
+    bool rel = true;
+    if (mech == 0) {
+        // Brooks-Herring: P(cos) ~ 1 / (2k^2 (1 - cos) + beta^2)^2
+        ct = Real(1) - Real(2) * u2 / (Real(1) + Real(4) * k2 * (Real(1) - u2) / ph.beta2);
+    } else if (mech <= 2) {
+        // Froehlich: P(cos) ~ 1 / (k^2 + k'^2 - 2 k k' cos)
+        const Real d = km - kp;
+        const Real xi = Real(2) * km * kp / (d * d);
+        ct = (xi >= Real(1e-6)) ? ((Real(1) + xi) - Mth<Real>::pow_(Real(1) + Real(2) * xi, u2)) / xi
+                                : Real(1) - Real(2) * u2;
+    } else {
+        ct = Real(1) - Real(2) * u2;  // isotropic
+        rel = false;
+    }
+    Real sp, cp;
+    Mth<Real>::sincos2pi_u(Q.u3, &sp, &cp);
+    const Real st = Mth<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
+    Real dx, dy, dz;
+    if (rel) {
+        // frame of k: branchless orthonormal basis (Duff et al., JCGT 2017)
+        Real nx = 0, ny = 0, nz = 1;
+        if (km > Real(0)) {
+            const Real ik = Real(1) / km;
+            nx = q.kx * ik;
+            ny = q.ky * ik;
+            nz = q.kz * ik;
+        }
+        const Real sg = copysign(Real(1), nz);
+        const Real aa = Real(-1) / (sg + nz);
+        const Real bb = nx * ny * aa;
+        const Real e1x = Real(1) + sg * nx * nx * aa, e1y = sg * bb, e1z = -sg * nx;
+        const Real e2x = bb, e2y = sg + ny * ny * aa, e2z = -ny;
+        const Real sc = st * cp, ss = st * sp;
+        dx = sc * e1x + ss * e2x + ct * nx;
+        dy = sc * e1y + ss * e2y + ct * ny;
+        dz = sc * e1z + ss * e2z + ct * nz;
+    } else {
+        dx = st * cp;
+        dy = st * sp;
+        dz = ct;
+    }
+    q.kx = kp * dx;
+    q.ky = kp * dy;
+    q.kz = kp * dz;
+    q.E = Ep;
+    const int w = q.e - e_base;
+    if (w >= 0 && w < WE)
+        atomicAdd(&bt->ev[w][v * NM + mech], 1u);
+    else
+        atomicAdd(&P.events[((size_t)q.e * NV + v) * NM + mech], 1ull);
+    if (NW && mech != 0 && mech != 3) {
+        const int c = cell_of<Real>(K, q.x, q.y, q.z);
+        // net emission: mech 1 absorbs, 2 emits; 4+2j absorbs, 5+2j emits
+        const long long d = (mech == 1) ? -1 : (mech == 2 ? 1 : ((mech & 1) ? 1 : -1));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.heat[((size_t)q.e * K.ncell + c) * 2 + (mech <= 2 ? 0 : 1)]),
+                  (unsigned long long)d);
+    }
+    q.v = j;
+    q.tr = Mth<Real>::neglog_u(Q.u1) * ph.inv_g0[j];
+}
 
-    Acc<Real> s_v[3], s_E, s_Et;
-    unsigned int n_v[NV] = {0u, 0u, 0u};
-    int e = e_base;
-    bool live = false;
-    if (p < P.n_slots) {
-        const uint32_t tg = P.tag[p];
-        e = int(tg >> 8);
-        live = (tg & 0xFFu) != DEAD;
-        if (live) {
-            Part<Real> q;
-            q.e = e;
-            q.v = int(tg & 0xFFu);
-            q.kx = static_cast<const Real*>(P.kx)[p];
-            q.ky = static_cast<const Real*>(P.ky)[p];
-            q.kz = static_cast<const Real*>(P.kz)[p];
-            if (NW) {
-                q.x = static_cast<const Real*>(P.x)[p];
-                q.y = static_cast<const Real*>(P.y)[p];
-                q.z = static_cast<const Real*>(P.z)[p];
-            }
-            q.tr = static_cast<const Real*>(P.tr)[p];
-            q.ctr = P.ctr[p];
-            q.id = P.id[p];
-            q.seed = P.seed[e];
-            const int ts = P.tabset[e];
-            const Phys<Real>* ph = static_cast<const Phys<Real>*>(P.phys) + ts;
-            const Real* tab_g = tab_all + (size_t)ts * NV * P.nb * NM;
-            const int nbs_e = (P.n_tab == 1) ? nbs : 0;
-            const Real dt = Real(P.dt);
-            Real a[3], ah[3] = {0, 0, 0}, inv_hF = 0;
-            if (!NW) {
-                const Real* ab = static_cast<const Real*>(P.acc_bulk) + 3 * (size_t)e;
-                a[0] = ab[0];
-                a[1] = ab[1];
-                a[2] = ab[2];
-            }
-            for (int s = 0; s < n_steps; ++s) {
-                if (NW) {
-                    const int c = cell_of<Real>(P, q.x, q.y, q.z);
-                    const Real* ac = static_cast<const Real*>(P.acc_cell) + 3 * ((size_t)e * P.ncell + c);
-                    a[0] = ac[0];
-                    a[1] = ac[1];
-                    a[2] = ac[2];
-                    const Real am = Mth<Real>::sqrt_(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-                    if (am > Real(0)) {
-                        ah[0] = a[0] / am;
-                        ah[1] = a[1] / am;
-                        ah[2] = a[2] / am;
-                        inv_hF = Real(1) / (Real(kHbarEVfs) * am);
-                    } else {
-                        inv_hF = Real(0);
-                    }
-                }
-                Real tleft = dt;
-                bool died = false;
-                for (int it = 0;; ++it) {
-                    if (it >= MAX_FLIGHTS_PER_STEP) {
-                        atomicOr(P.err, ERR_FLIGHTS);
-                        break;
-                    }
-                    if (q.tr >= tleft) {
-                        drift<Real, NW>(q, ph, a, ah, inv_hF, tleft);
-                        q.tr -= tleft;
-                        if (NW) died = walls(q, P, bt, e_base);
-                        break;
-                    }
-                    drift<Real, NW>(q, ph, a, ah, inv_hF, q.tr);
-                    tleft -= q.tr;
-                    if (NW && walls(q, P, bt, e_base)) {
-                        died = true;
-                        break;
-                    }
-                    scatter<Real, NW>(q, P, ph, tab_s, nbs_e, tab_g, bt, e_base);
-                }
-                if (died) {
-                    live = false;
-                    break;
-                }
-                const int v = q.v;
-                const Real E = kane_E(ph->ck[v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), ph->alpha[v]);
-                const Real f = ph->vk[v] / (Real(1) + Real(2) * ph->alpha[v] * E);
-                s_v[0].add(f * q.kx);
-                s_v[1].add(f * q.ky);
-                s_v[2].add(f * q.kz);
-                s_E.add(E);
-                s_Et.add(E + ph->Ec[v]);
-                n_v[v] += 1u;
-            }
-            store<Real>(P, p, q, NW);
-            P.tag[p] = (uint32_t(e) << 8) | (live ? uint32_t(q.v) : DEAD);
-            if (NW && count_charge && live) atomicAdd(&P.charge[(size_t)e * P.ncell + cell_of<Real>(P, q.x, q.y, q.z)], 1);
-        }
-    }
-    // ---- block reduction of the per-step samples
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    double vals[NSUM] = {s_v[0].value(), s_v[1].value(), s_v[2].value(), s_E.value(), s_Et.value(), 0.0, 0.0, 0.0};
-    unsigned int cnts[NV + 1] = {n_v[0], n_v[1], n_v[2], n_v[0] + n_v[1] + n_v[2]};
-    const int e0 = __shfl_sync(FULL, e, 0);
-    const bool uniform = __all_sync(FULL, e == e0);
-    if (uniform) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int i = 0; i < 5; ++i) vals[i] += __shfl_xor_sync(FULL, vals[i], o);
-#pragma unroll
-            for (int i = 0; i < NV + 1; ++i) cnts[i] += __shfl_xor_sync(FULL, cnts[i], o);
-        }
-    }
-    if (!uniform || lane == 0) {
-        if (cnts[NV] > 0u) {
+// Per-thread samples of one ensemble, flushed to the block window (or
+// global memory) when the thread moves on to another ensemble.
+template <typename Real>
+struct Samples {
+    Acc<Real> v[3], E, Et;
+    unsigned int nv[NV] = {0u, 0u, 0u};
+    int e = -1;
+
+    __device__ __forceinline__ void flush(const DevParams& P, BlockTally* bt, int e_base)
+    {
+        const unsigned int n = nv[0] + nv[1] + nv[2];
+        if (e >= 0 && n > 0u) {
+            const double vals[5] = {v[0].value(), v[1].value(), v[2].value(), E.value(), Et.value()};
             const int w = e - e_base;
             if (w >= 0 && w < WE) {
                 for (int i = 0; i < 5; ++i) atomicAdd(&bt->sums[w][i], vals[i]);
-                for (int i = 0; i < NV; ++i) atomicAdd(&bt->cnt[w][CNT_V0 + i], cnts[i]);
-                atomicAdd(&bt->cnt[w][CNT_SAMPLES], cnts[NV]);
+                for (int i = 0; i < NV; ++i) atomicAdd(&bt->cnt[w][CNT_V0 + i], nv[i]);
+                atomicAdd(&bt->cnt[w][CNT_SAMPLES], n);
             } else {
                 for (int i = 0; i < 5; ++i) atomicAdd(&P.sums[(size_t)e * NSUM + i], vals[i]);
-                for (int i = 0; i < NV; ++i)
-                    atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_V0 + i], (unsigned long long)cnts[i]);
-                atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_SAMPLES], (unsigned long long)cnts[NV]);
+                for (int i = 0; i < NV; ++i) atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_V0 + i], (unsigned long long)nv[i]);
+                atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_SAMPLES], (unsigned long long)n);
             }
         }
+        for (int i = 0; i < 3; ++i) v[i].clear();
+        E.clear();
+        Et.clear();
+        nv[0] = nv[1] = nv[2] = 0u;
     }
+};
+
+// -------------------------------------------------------------- flight
+// Persistent blocks; block b owns the slot range [b * per_block,
+// (b + 1) * per_block) and walks it one blockDim tile at a time (coalesced
+// state loads and stores); each thread advances its particle by n_steps time
+// steps.  Inside a step every iteration carries the particle to its next
+// event -- the end of the step or a scattering -- through one shared drift
+// and wall check, so the warp runs the drift once per iteration whatever
+// event each lane meets.  The rate table of a single table set is staged in
+// shared memory for bins [0, nbs); the per-table-set physics for up to 64
+// table sets.
+template <typename Real, bool NW>
+__global__ void __launch_bounds__(256, 3)
+    k_flight(const DevParams P, const KConst<Real> K, int n_steps, int count_charge)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nbs = K.nbs;
+    Real* tab_s = reinterpret_cast<Real*>(sm);
+    size_t off = ((size_t)NV * nbs * NM * sizeof(Real) + 15) & ~size_t(15);
+    Phys<Real>* ph_s = reinterpret_cast<Phys<Real>*>(sm + off);
+    off += ((size_t)K.n_tab_s * sizeof(Phys<Real>) + 15) & ~size_t(15);
+    BlockTally* bt = reinterpret_cast<BlockTally*>(sm + off);
+
+    const Real* tab_all = static_cast<const Real*>(P.table);
+    const Phys<Real>* ph_g = static_cast<const Phys<Real>*>(P.phys);
+    for (int i = threadIdx.x; i < NV * nbs * NM; i += blockDim.x) {
+        const int v = i / (nbs * NM), rr = i - v * nbs * NM;
+        tab_s[i] = tab_all[(size_t)v * K.nb * NM + rr];
+    }
+    for (int i = threadIdx.x; i < K.n_tab_s * (int)(sizeof(Phys<Real>) / sizeof(Real)); i += blockDim.x)
+        reinterpret_cast<Real*>(ph_s)[i] = reinterpret_cast<const Real*>(ph_g)[i];
+    for (int i = threadIdx.x; i < (int)(sizeof(BlockTally) / 4); i += blockDim.x)
+        reinterpret_cast<unsigned int*>(bt)[i] = 0u;
+    const int64_t b0 = (int64_t)blockIdx.x * K.per_block;
+    const int64_t b1 = min(b0 + K.per_block, P.n_slots);
+    const int e_base = b0 < P.n_slots ? int(P.tag[b0] >> 8) : 0;
+    __syncthreads();
+
+    const Real dt = K.dt;
+    const int nbs1 = (K.n_tab == 1) ? nbs : 0;
+    Samples<Real> S;
+    for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
+        const uint32_t tg = P.tag[p];
+        if ((tg & 0xFFu) == DEAD) continue;
+        QEntry<Real> Q;
+        Part<Real>& q = Q.q;
+        q.e = int(tg >> 8);
+        q.v = int(tg & 0xFFu);
+        if (q.e != S.e) {
+            S.flush(P, bt, e_base);
+            S.e = q.e;
+        }
+        q.kx = static_cast<const Real*>(P.kx)[p];
+        q.ky = static_cast<const Real*>(P.ky)[p];
+        q.kz = static_cast<const Real*>(P.kz)[p];
+        if (NW) {
+            q.x = static_cast<const Real*>(P.x)[p];
+            q.y = static_cast<const Real*>(P.y)[p];
+            q.z = static_cast<const Real*>(P.z)[p];
+        } else {
+            q.x = q.y = q.z = Real(0);
+        }
+        q.tr = static_cast<const Real*>(P.tr)[p];
+        q.ctr = P.ctr[p];
+        q.id = P.id[p];
+        q.seed = P.seed[q.e];
+        const int ts = P.tabset[q.e];
+        const Phys<Real>& ph = (ts < K.n_tab_s) ? ph_s[ts] : ph_g[ts];
+        const Real* tab_g = tab_all + (size_t)ts * NV * K.nb * NM;
+        q.E = kane_E(ph.ck[q.v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), ph.alpha[q.v]);
+        Real f4[4];
+        if (!NW) load4<Real>(static_cast<const Real*>(P.acc_bulk) + 4 * (size_t)q.e, f4);
+        bool live = true;
+        for (int s = 0; s < n_steps && live; ++s) {
+            if (NW)
+                load4<Real>(static_cast<const Real*>(P.acc_cell) +
+                                4 * ((size_t)q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z)), f4);
+            Real tleft = dt;
+            for (int it = 0;; ++it) {
+                if (it >= MAX_FLIGHTS_PER_STEP) {
+                    atomicOr(P.err, ERR_FLIGHTS);
+                    break;
+                }
+                const bool step_end = q.tr >= tleft;
+                drift<Real, NW>(q, ph, f4, step_end ? tleft : q.tr);
+                if (NW && walls(q, P, K, bt, e_base)) {
+                    live = false;
+                    break;
+                }
+                if (step_end) {
+                    q.tr -= tleft;
+                    break;
+                }
+                tleft -= q.tr;
+                if (choose<Real>(Q, P, K, ph, tab_s, nbs1, tab_g, bt, e_base) >= 0)
+                    final_state<Real, NW>(Q, P, K, ph, bt, e_base);
+            }
+            if (!live) break;
+            const int v = q.v;
+            const Real f = ph.vk[v] / (Real(1) + Real(2) * ph.alpha[v] * q.E);
+            S.v[0].add(f * q.kx);
+            S.v[1].add(f * q.ky);
+            S.v[2].add(f * q.kz);
+            S.E.add(q.E);
+            S.Et.add(q.E + ph.Ec[v]);
+            S.nv[v] += 1u;
+        }
+        store<Real>(P, p, q, NW);
+        P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
+        if (NW && count_charge && live)
+            atomicAdd(&P.charge[(size_t)q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z)], 1);
+    }
+    S.flush(P, bt, e_base);
     __syncthreads();
     for (int i = threadIdx.x; i < WE * NV * NM; i += blockDim.x) {
         const int w = i / (NV * NM), j = i - w * NV * NM;
@@ -539,7 +619,12 @@ __global__ void __launch_bounds__(512) k_flight(const DevParams P, int n_steps, 
     for (int i = threadIdx.x; i < WE * NCNT; i += blockDim.x) {
         const int w = i / NCNT, j = i - w * NCNT;
         const unsigned int n = bt->cnt[w][j];
-        if (n && e_base + w < P.n_ens) atomicAdd(&P.cnt[(size_t)(e_base + w) * NCNT + j], (unsigned long long)n);
+        if (n && e_base + w < P.n_ens) {
+            atomicAdd(&P.cnt[(size_t)(e_base + w) * NCNT + j], (unsigned long long)n);
+            if (j == CNT_SRC_OUT || j == CNT_DRN_OUT)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&P.alive[e_base + w]),
+                          (unsigned long long)(-(long long)n));
+        }
     }
     for (int i = threadIdx.x; i < WE * NSUM; i += blockDim.x) {
         const int w = i / NSUM, j = i - w * NSUM;
@@ -587,8 +672,14 @@ __global__ void k_init(const DevParams P)
 // --------------------------------------------------------------- inject
 // Refill each contact subcell (the x = 0 layer first, then x = Lx, cells in
 // (y, z) order) up to n_target electrons, taking free ids of the ensemble in
-// increasing order.  One block per ensemble; dynamic shared memory holds the
-// deficit prefix sums (2 ny nz + 1 ints) and a scan buffer (blockDim ints).
+// increasing order: the r-th free id fills the r-th missing electron.  One
+// block per ensemble.  Threads own contiguous words of the free-id bitmap;
+// a block scan of the words' population counts gives each free id its rank,
+// ids are gathered by rank into shared memory (INJ per round) and the new
+// electrons are drawn in parallel.  Dynamic shared memory: the deficit prefix
+// sums (2 ny nz + 1 ints), a scan buffer (blockDim ints) and INJ ids.
+constexpr int INJ = 1024;
+
 template <typename Real>
 __global__ void __launch_bounds__(256) k_inject(const DevParams P)
 {
@@ -597,6 +688,8 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
     const int nface = P.ny * P.nz, ncon = 2 * nface;
     int* pre = shi;
     int* scan = shi + ncon + 1;
+    uint32_t* ids = reinterpret_cast<uint32_t*>(scan + blockDim.x);
+    __shared__ int n_src, n_drn;
     if (threadIdx.x == 0) {
         int acc = 0;
         pre[0] = 0;
@@ -608,6 +701,8 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
             acc += need > 0 ? need : 0;
             pre[t + 1] = acc;
         }
+        n_src = 0;
+        n_drn = 0;
     }
     __syncthreads();
     const int D = pre[ncon];
@@ -619,7 +714,6 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
     const int64_t w1 = w0 + per < words ? w0 + per : words;
     int mine = 0;
     for (int64_t w = w0; w < w1; ++w) mine += __popc(bits[w]);
-    // block exclusive scan
     scan[threadIdx.x] = mine;
     __syncthreads();
     for (int off = 1; off < (int)blockDim.x; off <<= 1) {
@@ -629,23 +723,33 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
         __syncthreads();
     }
     const int total = scan[blockDim.x - 1];
-    int rank = scan[threadIdx.x] - mine;
+    const int base = scan[threadIdx.x] - mine;
+    const int Deff = D < total ? D : total;
     if (threadIdx.x == 0 && total < D)
         atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_STARVED], (unsigned long long)(D - total));
     const Phys<Real>* ph = static_cast<const Phys<Real>*>(P.phys) + P.tabset[e];
     const Real len3[3] = {Real(P.dx), Real(P.dy), Real(P.dz)};
-    for (int64_t w = w0; w < w1 && rank < D; ++w) {
-        uint32_t word = bits[w];
-        uint32_t clear = 0u;
-        while (word && rank < D) {
-            const int bit = __ffs(word) - 1;
-            word &= word - 1u;
-            const uint32_t id = uint32_t(w * 32 + bit);
-            // contact t with pre[t] <= rank < pre[t + 1]
-            int lo = 0, hi = ncon - 1;
+    for (int r0 = 0; r0 < Deff; r0 += INJ) {
+        const int r1 = min(Deff, r0 + INJ);
+        // gather the ids of ranks [r0, r1) by rank
+        int rank = base;
+        for (int64_t w = w0; w < w1 && rank < r1; ++w) {
+            uint32_t word = bits[w];
+            while (word && rank < r1) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1u;
+                if (rank >= r0) ids[rank - r0] = uint32_t(w * 32 + bit);
+                ++rank;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) {
+            const int rk = r0 + i;
+            const uint32_t id = ids[i];
+            int lo = 0, hi = ncon - 1;  // contact t with pre[t] <= rk < pre[t + 1]
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (pre[mid] <= rank) lo = mid;
+                if (pre[mid] <= rk) lo = mid;
                 else hi = mid - 1;
             }
             const int t = lo;
@@ -662,19 +766,35 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
             store<Real>(P, slot, q, true);
             P.tag[slot] = uint32_t(e) << 8;
             atomicAdd(&P.charge[(size_t)e * P.ncell + ix * nface + rem], 1);
-            atomicAdd(&P.cnt[(size_t)e * NCNT + (side ? CNT_DRN_IN : CNT_SRC_IN)], 1ull);
+            atomicAdd(side ? &n_drn : &n_src, 1);
+        }
+        __syncthreads();
+    }
+    // clear the bits of the ids taken (ranks below Deff)
+    int rank = base;
+    for (int64_t w = w0; w < w1 && rank < Deff; ++w) {
+        uint32_t word = bits[w], clear = 0u;
+        while (word && rank < Deff) {
+            const int bit = __ffs(word) - 1;
+            word &= word - 1u;
             clear |= 1u << bit;
             ++rank;
         }
         bits[w] &= ~clear;
     }
+    if (threadIdx.x == 0) {
+        atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_SRC_IN], (unsigned long long)n_src);
+        atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_DRN_IN], (unsigned long long)n_drn);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.alive[e]), (unsigned long long)(n_src + n_drn));
+    }
 }
 
 // --------------------------------------------------------------- launch
 template <typename Real>
-size_t flight_smem_bytes(int nb_smem)
+size_t flight_smem_bytes(int nb_smem, int n_tab_s)
 {
-    return (((size_t)NV * nb_smem * NM * sizeof(Real) + 15) & ~size_t(15)) + sizeof(BlockTally);
+    return (((size_t)NV * nb_smem * NM * sizeof(Real) + 15) & ~size_t(15)) +
+           (((size_t)n_tab_s * sizeof(Phys<Real>) + 15) & ~size_t(15)) + sizeof(BlockTally);
 }
 
 template <typename Real>
@@ -685,18 +805,51 @@ cudaError_t flight_set_smem(size_t bytes)
     return cudaFuncSetAttribute(k_flight<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// resident flight blocks per SM for this shared-memory size
 template <typename Real>
-void launch_flight(const DevParams& P, bool nw, int n_steps, int count_charge, int block, cudaStream_t st)
+int flight_blocks_per_sm(bool nw, int block, size_t smem)
 {
-    if (P.n_slots <= 0) return;
-    const unsigned grid = (unsigned)((P.n_slots + block - 1) / block);
-    const size_t smem = flight_smem_bytes<Real>(P.nb_smem);
+    int n = 0;
     if (nw)
-        k_flight<Real, true><<<grid, block, smem, st>>>(P, n_steps, count_charge);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_flight<Real, true>, block, smem);
     else
-        k_flight<Real, false><<<grid, block, smem, st>>>(P, n_steps, count_charge);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_flight<Real, false>, block, smem);
+    return n > 0 ? n : 1;
 }
 
+template <typename Real>
+void launch_flight(const DevParams& P, bool nw, int n_steps, int count_charge, int block, int grid_cap,
+                   cudaStream_t st)
+{
+    if (P.n_slots <= 0) return;
+    KConst<Real> K;
+    K.Lx = Real(P.Lx);
+    K.Ly = Real(P.Ly);
+    K.Lz = Real(P.Lz);
+    K.inv_dx = Real(1.0 / P.dx);
+    K.inv_dy = Real(1.0 / P.dy);
+    K.inv_dz = Real(1.0 / P.dz);
+    K.p_spec = Real(P.p_spec);
+    K.dt = Real(P.dt);
+    K.inv_dE = Real(P.inv_dE);
+    K.nx = P.nx;
+    K.ny = P.ny;
+    K.nz = P.nz;
+    K.ncell = P.ncell;
+    K.nb = P.nb;
+    K.nbs = P.nb_smem;
+    K.n_tab = P.n_tab;
+    K.n_tab_s = P.n_tab <= 64 ? P.n_tab : 0;
+    const int64_t tiles = (P.n_slots + block - 1) / block;
+    const int64_t grid = tiles < grid_cap ? tiles : grid_cap;
+    K.per_block = ((P.n_slots + grid - 1) / grid + 31) / 32 * 32;
+    const int64_t g = (P.n_slots + K.per_block - 1) / K.per_block;
+    const size_t smem = flight_smem_bytes<Real>(K.nbs, K.n_tab_s);
+    if (nw)
+        k_flight<Real, true><<<(unsigned)g, block, smem, st>>>(P, K, n_steps, count_charge);
+    else
+        k_flight<Real, false><<<(unsigned)g, block, smem, st>>>(P, K, n_steps, count_charge);
+}
 template <typename Real>
 void launch_init(const DevParams& P, bool nw, cudaStream_t st)
 {
@@ -712,7 +865,7 @@ template <typename Real>
 void launch_inject(const DevParams& P, cudaStream_t st)
 {
     const int block = 256;
-    const size_t smem = sizeof(int) * (2 * P.ny * P.nz + 1 + block);
+    const size_t smem = sizeof(int) * (2 * P.ny * P.nz + 1 + block + INJ);
     k_inject<Real><<<P.n_ens, block, smem, st>>>(P);
 }
 

@@ -46,7 +46,7 @@ class EmcConfig(C.Structure):
         ("steps_per_poisson", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
         ("gate_on", C.c_int32), ("seed", C.c_uint32), ("mech_mask", C.c_uint32),
         ("precision", C.c_int32), ("sort_period", C.c_int32), ("block_size", C.c_int32),
-        ("steps_per_launch", C.c_int32),
+        ("steps_per_launch", C.c_int32), ("table_smem_kb", C.c_int32),
     ]
 
 
@@ -77,6 +77,9 @@ def lib():
         L.emc_tally.argtypes = [P, I32, P, C.c_size_t, I32, I32]
         L.poisson_solve.argtypes = [P, dp, dp, dp]
         L.emc_set_bias.argtypes = [P, I32, C.c_double, C.c_double, C.c_double]
+        L.emc_set_bias_all.argtypes = [P, dp]
+        L.emc_profile.argtypes = [P, I32]
+        L.emc_profile_read.argtypes = [P, dp, C.POINTER(I64)]
         L.emc_debug_philox.argtypes = [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32), I32]
         L.emc_debug_particles.argtypes = [P, dp, dp, dp, C.POINTER(I32), C.POINTER(I32), C.POINTER(U32),
                                           C.POINTER(C.c_uint64)]
@@ -88,6 +91,7 @@ def lib():
         L.emc_last_error.restype = C.c_char_p
         L.emc_destroy.argtypes = [P]
         for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "poisson_solve", "emc_set_bias",
+                  "emc_set_bias_all", "emc_profile", "emc_profile_read",
                   "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -119,6 +123,7 @@ def make_config(d: dict, precision: int = FP32) -> EmcConfig:
     c.sort_period = d.get("sort_period", 0)
     c.block_size = d.get("block_size", 0)
     c.steps_per_launch = d.get("steps_per_launch", 0)
+    c.table_smem_kb = d.get("table_smem_kb", 0)
     return c
 
 
@@ -206,6 +211,22 @@ class Context:
 
     def emc_set_bias(self, ens: int, Vs: float, Vd: float, Vg: float):
         self._check(lib().emc_set_bias(self.h, int(ens), Vs, Vd, Vg))
+
+    def emc_set_bias_all(self, bias_ptr_or_array):
+        """bias: host float64 [E][3] (numpy array, or an int address of pinned memory)."""
+        if isinstance(bias_ptr_or_array, int):
+            self._check(lib().emc_set_bias_all(self.h, C.cast(C.c_void_p(bias_ptr_or_array), C.POINTER(C.c_double))))
+        else:
+            b = np.ascontiguousarray(bias_ptr_or_array, dtype=np.float64).reshape(self.n_ens, 3)
+            self._check(lib().emc_set_bias_all(self.h, _p(b)))
+
+    def emc_profile(self, enable: bool):
+        self._check(lib().emc_profile(self.h, int(enable)))
+
+    def emc_profile_read(self):
+        ms, n = C.c_double(), C.c_int64()
+        self._check(lib().emc_profile_read(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def debug_philox(self, ctr, key):
         ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)

@@ -171,6 +171,26 @@ emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes,
 emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null,
                          const double* bc_volts, double* phi_out_or_null);
 
+/* Allocation-free variant of poisson_solve (the paper has no counterpart;
+ * this entry point exists for callers that must not allocate device memory,
+ * e.g. a host that has reserved the whole device for its own pool, or code
+ * that runs where allocation is forbidden or must not be recorded).  Same
+ * arguments, result and accuracy as poisson_solve, but its temporaries (the
+ * right-hand side, the potential, the charge density, the voltages and the
+ * residual) live in one static device array of about 229 KiB owned by the
+ * library, so the call performs no cudaMalloc/cudaFree of its own.
+ *  - Limit: at most 8192 subcells; larger grids return EMC_EINVAL.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.  The array then stays reserved on every
+ *    device that used it until the library is unloaded.
+ *  - All calls share the one array: calls that may overlap on the GPU
+ *    (other threads, other streams, other contexts on the same device) race
+ *    and must be serialised by the caller.  Each call zeroes the potential
+ *    it starts from, so a call never sees the previous call's result. */
+emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null,
+                                    const double* bc_volts, double* phi_out_or_null);
+
 /* Set the terminal voltages of ensemble ens and re-solve its field. */
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg);
 

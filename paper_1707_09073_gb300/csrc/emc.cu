@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/emc.h"
@@ -1045,6 +1046,87 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
     CK(cudaFreeAsync(phi, ctx->st));
     CK(cudaFreeAsync(bias, ctx->st));
     CK(cudaFreeAsync(r32, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------- allocation-free Poisson solve
+// Scratch of emc_poisson_solve_static: right-hand side, potential and charge
+// density (double[kStaticCells] each), the three terminal voltages, and the
+// float residual, in one file-scope device array that lives as long as the
+// library is loaded on each device that uses it.
+namespace {
+constexpr int kStaticCells = 8192;
+constexpr size_t kStaticDoubles = 3 * (size_t)kStaticCells + 4 + kStaticCells / 2;
+static __device__ __align__(256) double g_poisson_scratch[kStaticDoubles];
+
+// device address of the scratch array, looked up once per device with that
+// device current (the host-side symbol itself is not a device address)
+std::mutex g_scratch_mu;
+void* g_scratch_addr[128] = {nullptr};
+
+emc_status static_scratch(emc_ctx* ctx, double** out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return fail(ctx, EMC_EINVAL, "device ordinal out of range for the static scratch");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_poisson_scratch));
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<double*>(g_scratch_addr[dev]);
+    return EMC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, const double* bc_volts,
+                                    double* phi_out_or_null)
+{
+    if (!ctx || !bc_volts) return EMC_EINVAL;
+    if (ctx->geom != EMC_GEOM_NANOWIRE)
+        return fail(ctx, EMC_ESTATE, "emc_poisson_solve_static needs the nanowire geometry");
+    const int n = ctx->ncell;
+    if (n > kStaticCells) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "emc_poisson_solve_static: %d subcells exceed its static scratch limit of %d", n,
+                 kStaticCells);
+        return fail(ctx, EMC_EINVAL, buf);
+    }
+    double* base = nullptr;
+    emc_status st = static_scratch(ctx, &base);
+    if (st != EMC_OK) return st;
+    double* rhs = base;
+    double* phi = base + kStaticCells;
+    double* rho = base + 2 * (size_t)kStaticCells;
+    double* bias = base + 3 * (size_t)kStaticCells;
+    float* r32 = reinterpret_cast<float*>(base + 3 * (size_t)kStaticCells + 4);
+    // the previous call's contents are still there: start the potential at zero
+    CK(cudaMemsetAsync(phi, 0, 8 * (size_t)n, ctx->st));
+    CK(cudaMemcpyAsync(bias, bc_volts, 24, cudaMemcpyHostToDevice, ctx->st));
+    PoisGeo G = pgeo(ctx);
+    const double Vcell = ctx->dx * ctx->dy * ctx->dz;
+    if (charge_or_null) {
+        CK(cudaMemcpyAsync(rho, charge_or_null, 8 * (size_t)n, cudaMemcpyHostToDevice, ctx->st));
+        k_rhs<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, nullptr, rho, ctx->d_w, ctx->d_Nd, Vcell,
+                                                     kE2Eps0 / ctx->cfg[0].eps_s, bias, rhs);
+    } else {
+        k_rhs<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, ctx->charge, nullptr, ctx->d_w, ctx->d_Nd, Vcell,
+                                                     kE2Eps0 / ctx->cfg[0].eps_s, bias, rhs);
+    }
+    for (int sw = 0; sw < kPoissonSweeps + 2; ++sw) {
+        k_resid<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, rhs, phi, r32);
+        k_sweep<<<dim3(grid_for(n, 16), 1), 256, 0, ctx->st>>>(ctx->G32, r32, phi, n, 1);
+    }
+    ctx->launches += 1 + 2 * (kPoissonSweeps + 2);
+    CK(cudaGetLastError());
+    if (phi_out_or_null)
+        CK(cudaMemcpyAsync(phi_out_or_null, phi, 8 * (size_t)n, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
 }

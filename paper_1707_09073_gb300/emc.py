@@ -76,6 +76,7 @@ def lib():
         L.emc_step.argtypes = [P, I32]
         L.emc_tally.argtypes = [P, I32, P, C.c_size_t, I32, I32]
         L.poisson_solve.argtypes = [P, dp, dp, dp]
+        L.emc_poisson_solve_static.argtypes = [P, dp, dp, dp]
         L.emc_set_bias.argtypes = [P, I32, C.c_double, C.c_double, C.c_double]
         L.emc_set_bias_all.argtypes = [P, dp]
         L.emc_profile.argtypes = [P, I32]
@@ -90,7 +91,8 @@ def lib():
         L.emc_last_error.argtypes = [P]
         L.emc_last_error.restype = C.c_char_p
         L.emc_destroy.argtypes = [P]
-        for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "poisson_solve", "emc_set_bias",
+        for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "poisson_solve",
+                  "emc_poisson_solve_static", "emc_set_bias",
                   "emc_set_bias_all", "emc_profile", "emc_profile_read",
                   "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape"):
             getattr(L, f).restype = C.c_int
@@ -207,6 +209,15 @@ class Context:
         phi = np.zeros(self.n_cell)
         ch = None if charge is None else np.ascontiguousarray(charge, dtype=np.float64)
         self._check(lib().poisson_solve(self.h, _p(ch) if ch is not None else None, _p(bc), _p(phi)))
+        return phi
+
+    def emc_poisson_solve_static(self, charge=None, bc_volts=(0.0, 0.0, 0.0)):
+        """poisson_solve without device allocation (library-owned static scratch,
+        at most 8192 subcells; calls must not overlap on the GPU)."""
+        bc = np.ascontiguousarray(bc_volts, dtype=np.float64)
+        phi = np.zeros(self.n_cell)
+        ch = None if charge is None else np.ascontiguousarray(charge, dtype=np.float64)
+        self._check(lib().emc_poisson_solve_static(self.h, _p(ch) if ch is not None else None, _p(bc), _p(phi)))
         return phi
 
     def emc_set_bias(self, ens: int, Vs: float, Vd: float, Vg: float):

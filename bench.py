@@ -37,12 +37,19 @@ UNIT = "events/s"
 STEPS_PER_POISSON = 10
 N_SM = 152
 LANES_PER_SM = 128
-# Algorithmic operation model of the flight kernel (lane operations):
-#   per real scattering: ~150 FP32 (energy, final state, angle law, rotation)
-#   + ~60 integer (one Philox4x32-10 call);
-#   per self-scattering: ~40 FP32 (energy, bin, table scan, flight time) + ~60 Philox;
-#   per particle-step: ~40 FP32 (free flight and the step sample).
-OPS_REAL, OPS_SELF, OPS_STEP = 210, 100, 40
+# Algorithmic operation model of the flight kernel: lane operations (FP32,
+# integer and special-function instructions of the method's arithmetic; no
+# loads, stores, address arithmetic or loop control), counted from the
+# kernel source for the nanowire geometry:
+#   per particle-step 98: subcell lookup 14, drift 44 (k, Kane energy, two
+#     group velocities, trapezoid + along-field correction, position), wall
+#     and contact tests 10, step end 2, the compensated step sample 28;
+#   per scattering (self or real) 133: another drift + wall test 54, Philox
+#     4x32-10 60, four uniforms 12, energy bin 5, first table compare 2;
+#   plus 6 for a self-scattering (tally, flight time) or 70 for a real one
+#     (table scan, final energy and |k'|, angle law, sin/cos, orthonormal
+#     basis and rotation, tallies, flight time).
+OPS_STEP, OPS_SELF, OPS_REAL = 98, 133 + 6, 133 + 70
 
 
 def sweep_configs(rank: int, n_particles: int, **tune) -> list[dict]:
@@ -71,7 +78,7 @@ def kernel_sha() -> str:
 def committed_traffic() -> float | None:
     """DRAM bytes per flight launch from the committed ncu summary, if it was
     taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "flight_traffic.json")
+    p = os.path.join(ROOT, "profiles", "flight_traffic.txt")
     try:
         with open(p) as f:
             d = json.load(f)
@@ -293,7 +300,8 @@ def run_emc(args, world: int, rank: int, local: int):
             "peak_basis": "152 SMs x 128 lanes x %.0f MHz max SM clock (lane operations/s)" % peaks.get("sm_max_mhz", 2070.0),
             "frac_at_sampled_clock": achieved / (N_SM * LANES_PER_SM * clk * 1e6 / 1e12),
             "flight_share_of_step": flight_ms / ms if ms > 0 else None,
-            "op_model": {"per_real_event": OPS_REAL, "per_self_event": OPS_SELF, "per_particle_step": OPS_STEP}}
+            "op_model": {"per_real_event": OPS_REAL, "per_self_event": OPS_SELF, "per_particle_step": OPS_STEP,
+                         "unit": "lane operations of the method's arithmetic (loads/addressing excluded)"}}
 
     # ---- oracle on the host cores (bounded sample)
     cpu = None

@@ -216,7 +216,15 @@ def run_emc(args, world: int, rank: int, local: int):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     n_part = args.particles
-    tune = {k: v for k, v in (("table_smem_kb", args.table_kb), ("block_size", args.block)) if v}
+    tune = {k: v for k, v in (("table_smem_kb", args.table_kb), ("block_size", args.block),
+                              ("sort_period", args.sort_period)) if v}
+    tuned = None
+    if not tune and not args.no_tune:
+        # block size, staged table size and sort period from the autotuner
+        # (timed once per GPU and workload shape, then cached)
+        from paper_1707_09073_gb300 import autotune
+        tuned = autotune.tune(sweep_configs(rank, n_part))
+        tune = dict(tuned)
     cfgs = sweep_configs(rank, n_part, **tune)
     E = len(cfgs)
     ctx = emc.Context(cfgs, stream=stream.cuda_stream)
@@ -315,6 +323,7 @@ def run_emc(args, world: int, rank: int, local: int):
 
     cfg = workload_desc(n_part)
     cfg["parallelism"] = "weak: one full sweep per GPU" if world > 1 else "1 GPU"
+    cfg["launch"] = dict(tune, source="autotuner" if tuned else ("command line" if tune else "defaults"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -345,6 +354,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--table-kb", type=int, default=0, help="rate-table KiB staged in shared memory (0 = default)")
     ap.add_argument("--block", type=int, default=0, help="flight-kernel block size (0 = default)")
+    ap.add_argument("--sort-period", type=int, default=0, help="sort particles every this many launches (0 = never)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

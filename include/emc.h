@@ -176,9 +176,10 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null,
  * e.g. a host that has reserved the whole device for its own pool, or code
  * that runs where allocation is forbidden or must not be recorded).  Same
  * arguments, result and accuracy as poisson_solve, but its temporaries (the
- * right-hand side, the potential, the charge density, the voltages and the
- * residual) live in one static device array of about 229 KiB owned by the
- * library, so the call performs no cudaMalloc/cudaFree of its own.
+ * right-hand side, the potential, the charge density, the voltages, the
+ * residual and the partial sums of the sweep) live in one static device
+ * array of about 1.6 MiB owned by the library, so the call performs no
+ * cudaMalloc or cudaFree of its own.
  *  - Limit: at most 8192 subcells; larger grids return EMC_EINVAL.
  *  - The first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress) with that device current; make that first call

@@ -11,7 +11,7 @@ namespace emc {
 
 constexpr int NV = 3;   // Gamma1, U, Gamma3
 constexpr int NM = 10;  // mechanisms per valley (see include/emc.h)
-constexpr int WE = 4;   // ensembles covered by a block's shared-memory tallies
+constexpr int WE = 32;  // ensembles with shared-memory block tallies (by index)
 constexpr uint32_t DEAD = 0xFFu;
 constexpr int MAX_FLIGHTS_PER_STEP = 1 << 16;
 constexpr int MAX_INIT_TRIALS = 1000;

@@ -20,6 +20,9 @@ template <typename Real> void launch_inject(const DevParams&, cudaStream_t);
 template <typename Real> cudaError_t flight_set_smem(size_t);
 template <typename Real> size_t flight_smem_bytes(int, int);
 template <typename Real> int flight_blocks_per_sm(bool, int, size_t);
+template <typename Real>
+void launch_sort(const DevParams&, const DevParams&, bool, uint32_t*, unsigned int*, const unsigned int*, unsigned int*,
+                 int, cudaStream_t);
 }  // namespace emc
 
 using namespace emc;
@@ -91,9 +94,22 @@ struct emc_ctx {
     // Poisson
     double *Lmat = nullptr, *Ginv = nullptr, *phi = nullptr, *rhs = nullptr, *Efield = nullptr, *d_bias = nullptr,
            *d_w = nullptr, *d_Nd = nullptr;
-    float *G32 = nullptr, *r32 = nullptr;
+    float *G32 = nullptr, *r32 = nullptr, *part = nullptr;
     uint8_t* d_gate = nullptr;
     std::vector<void*> allocs;
+    // particle sort (allocated on first use)
+    void *akx = nullptr, *aky = nullptr, *akz = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr, *atr = nullptr;
+    uint32_t *atag = nullptr, *aid = nullptr, *skey = nullptr;
+    uint64_t* actr = nullptr;
+    unsigned int *shist = nullptr, *soffs = nullptr, *sblk = nullptr;
+    int64_t n_keys = 0;
+    int64_t flights_since_sort = 0;
+    int64_t sorts = 0;
+    // graph of the per-chunk tail (refill + Poisson update + field)
+    cudaGraph_t g_tail = nullptr;
+    cudaGraphExec_t g_tail_exec = nullptr;
+    int64_t g_tail_launches = 0;
+    bool use_graph = true;
     // flight-kernel timing
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -308,45 +324,80 @@ __global__ void k_resid(PoisGeo G, int n_ens, const double* rhs, const double* p
     r32[i] = float(rhs[i] - acc);
 }
 
-// phi[e] += Ginv r[e] for 32 ensembles per grid column: a block owns 16 rows
-// (two per warp), lane = ensemble; G rows and r are staged through shared
-// memory in chunks of 64 columns.  Deterministic (no atomics).
-__global__ void __launch_bounds__(256) k_sweep(const float* G32, const float* r32, double* phi, int n, int n_ens)
+// phi[e] += Ginv r[e] as a skinny FP32 GEMM: tiles of 64 rows x 32
+// ensembles, the columns split into slices of 192 (grid.y) for parallelism.
+// A block stages 32 columns of its 64 rows of G (transposed, so a warp reads
+// its 8 rows as two broadcast float4) and of the 32 residual vectors in
+// shared memory; warp w owns rows 8w..8w+7, lane = ensemble.  Partial sums go
+// to part[slice][e][row] and k_sweep_reduce adds them in a fixed order
+// (deterministic).
+constexpr int kSweepRows = 64, kSweepSlice = 192;
+
+__global__ void __launch_bounds__(256) k_sweep(const float* __restrict__ G32, const float* __restrict__ r32,
+                                               float* part, int n, int n_ens, int ldp)
 {
-    constexpr int KC = 64, RB = 16;
-    __shared__ float Gs[RB][KC];
-    __shared__ float Rs[KC][33];
+    __shared__ __align__(16) float Gt[32][kSweepRows];  // [column][row]
+    __shared__ float Rs[32][33];                        // [column][ensemble]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = blockIdx.x * RB + 2 * warp;
-    const int e0 = blockIdx.y * 32;
-    const int ne = min(32, n_ens - e0);
-    float a[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (int k0 = 0; k0 < n; k0 += KC) {
-        for (int i = threadIdx.x; i < RB * KC; i += blockDim.x) {
-            const int rr = i / KC, kk = i - rr * KC;
-            const int gr = blockIdx.x * RB + rr, gk = k0 + kk;
-            Gs[rr][kk] = (gr < n && gk < n) ? G32[(size_t)gr * n + gk] : 0.f;
+    const int r0 = blockIdx.x * kSweepRows;
+    const int k_beg = blockIdx.y * kSweepSlice;
+    const int k_end = min(n, k_beg + kSweepSlice);
+    const int e0 = blockIdx.z * 32;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k0 = k_beg; k0 < k_end; k0 += 32) {
+        for (int i = threadIdx.x; i < kSweepRows * 32; i += blockDim.x) {
+            const int rr = i >> 5, kk = i & 31;  // coalesced along a row of G
+            const int gr = r0 + rr, gk = k0 + kk;
+            Gt[kk][rr] = (gr < n && gk < k_end) ? G32[(size_t)gr * n + gk] : 0.f;
         }
-        for (int i = threadIdx.x; i < 32 * KC; i += blockDim.x) {
-            const int ee = i / KC, kk = i - ee * KC;
+        for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+            const int ee = i >> 5, kk = i & 31;
             const int gk = k0 + kk;
-            Rs[kk][ee] = (ee < ne && gk < n) ? r32[(size_t)(e0 + ee) * n + gk] : 0.f;
+            Rs[kk][ee] = (e0 + ee < n_ens && gk < k_end) ? r32[(size_t)(e0 + ee) * n + gk] : 0.f;
         }
         __syncthreads();
 #pragma unroll 8
-        for (int kk = 0; kk < KC; kk += 2) {
-            const float r0 = Rs[kk][lane], r1 = Rs[kk + 1][lane];
-            a[0][0] += Gs[2 * warp][kk] * r0;
-            a[0][1] += Gs[2 * warp][kk + 1] * r1;
-            a[1][0] += Gs[2 * warp + 1][kk] * r0;
-            a[1][1] += Gs[2 * warp + 1][kk + 1] * r1;
+        for (int kk = 0; kk < 32; ++kk) {
+            const float rv = Rs[kk][lane];
+            const float4 ga = *reinterpret_cast<const float4*>(&Gt[kk][8 * warp]);
+            const float4 gb = *reinterpret_cast<const float4*>(&Gt[kk][8 * warp + 4]);
+            acc[0] += ga.x * rv;
+            acc[1] += ga.y * rv;
+            acc[2] += ga.z * rv;
+            acc[3] += ga.w * rv;
+            acc[4] += gb.x * rv;
+            acc[5] += gb.y * rv;
+            acc[6] += gb.z * rv;
+            acc[7] += gb.w * rv;
         }
         __syncthreads();
     }
-    if (lane < ne) {
-        if (row0 < n) phi[(size_t)(e0 + lane) * n + row0] += double(a[0][0] + a[0][1]);
-        if (row0 + 1 < n) phi[(size_t)(e0 + lane) * n + row0 + 1] += double(a[1][0] + a[1][1]);
-    }
+    const int e = e0 + lane;
+    if (e < n_ens)
+        for (int i = 0; i < 8; ++i) {
+            const int row = r0 + 8 * warp + i;
+            if (row < n) part[((size_t)blockIdx.y * ldp + e) * n + row] = acc[i];
+        }
+}
+
+__global__ void k_sweep_reduce(const float* part, double* phi, int n, int n_ens, int ldp, int slices)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_ens * n) return;
+    double s = 0.0;
+    for (int sl = 0; sl < slices; ++sl) s += double(part[(size_t)sl * ldp * n + i]);
+    phi[i] += s;
+}
+
+int sweep_slices(int n) { return (n + kSweepSlice - 1) / kSweepSlice; }
+
+// part must hold sweep_slices(n) * n_ens * n floats
+void launch_sweep(const float* G32, const float* r32, float* part, double* phi, int n, int n_ens, cudaStream_t st)
+{
+    const dim3 grid((n + kSweepRows - 1) / kSweepRows, sweep_slices(n), (n_ens + 31) / 32);
+    k_sweep<<<grid, 256, 0, st>>>(G32, r32, part, n, n_ens, n_ens);
+    k_sweep_reduce<<<(unsigned)(((int64_t)n_ens * n + 255) / 256), 256, 0, st>>>(part, phi, n, n_ens, n_ens,
+                                                                                 sweep_slices(n));
 }
 
 // E = -grad phi (V/nm): central differences, one-sided in boundary cells.
@@ -588,6 +639,7 @@ emc_status poisson_setup(emc_ctx* ctx)
     CK(dalloc(ctx, &ctx->phi, (size_t)ctx->n_ens * n));
     CK(dalloc(ctx, &ctx->rhs, (size_t)ctx->n_ens * n));
     CK(dalloc(ctx, &ctx->r32, (size_t)ctx->n_ens * n));
+    CK(dalloc(ctx, &ctx->part, (size_t)sweep_slices(n) * ctx->n_ens * n));
     CK(dalloc(ctx, &ctx->Efield, (size_t)ctx->n_ens * n * 3));
     CK(dalloc(ctx, &ctx->d_gate, (size_t)ctx->nx));
     CK(dalloc(ctx, &ctx->d_bias, (size_t)ctx->n_ens * 3));
@@ -633,12 +685,11 @@ emc_status poisson_update(emc_ctx* ctx)
                                                    kE2Eps0 / ctx->cfg[0].eps_s, ctx->d_bias, ctx->rhs);
     for (int s = 0; s < kPoissonSweeps; ++s) {
         k_resid<<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->rhs, ctx->phi, ctx->r32);
-        dim3 grd(grid_for(n, 16), grid_for(E, 32));
-        k_sweep<<<grd, 256, 0, ctx->st>>>(ctx->G32, ctx->r32, ctx->phi, n, E);
+        launch_sweep(ctx->G32, ctx->r32, ctx->part, ctx->phi, n, E, ctx->st);
     }
     k_field<Real><<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->phi, ctx->dx, ctx->dy, ctx->dz, ctx->Efield,
                                                            static_cast<Real*>(ctx->acc_cell));
-    ctx->launches += 2 + 2 * kPoissonSweeps;
+    ctx->launches += 2 + 3 * kPoissonSweeps;
     CK(cudaGetLastError());
     return EMC_OK;
 }
@@ -671,6 +722,104 @@ void fill_params(emc_ctx* ctx)
     const int kib = ctx->cfg[0].table_smem_kb > 0 ? ctx->cfg[0].table_smem_kb : kSmemTableKiB;
     int nbs = (ctx->n_tab == 1) ? (int)std::min<size_t>((size_t)ctx->nb, (size_t)kib * 1024 / row) : 0;
     P.nb_smem = nbs;
+}
+
+// exclusive scan of n uint32 (n <= 2048 * 2048): per-block scans of 2048
+// elements, a one-block scan of the block totals, then the block offsets
+__global__ void k_scan_blocks(const unsigned int* in, unsigned int* out, unsigned int* blk, int64_t n)
+{
+    __shared__ unsigned int sh[2048];
+    const int64_t base = (int64_t)blockIdx.x * 2048;
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) sh[i] = (base + i < n) ? in[base + i] : 0u;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over 2048 with 1024 threads (2 per thread)
+    for (int off = 1; off < 2048; off <<= 1) {
+        unsigned int a = 0, b = 0;
+        const int i0 = threadIdx.x, i1 = threadIdx.x + 1024;
+        if (i0 >= off) a = sh[i0 - off];
+        if (i1 >= off) b = sh[i1 - off];
+        __syncthreads();
+        sh[i0] += a;
+        sh[i1] += b;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+        if (base + i < n) out[base + i] = (i == 0 ? 0u : sh[i - 1]);
+    if (threadIdx.x == 0) blk[blockIdx.x] = sh[2047];
+}
+
+__global__ void k_scan_add(unsigned int* out, const unsigned int* blk, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] += blk[i / 2048];
+}
+
+template <typename Real>
+emc_status sort_particles(emc_ctx* ctx)
+{
+    const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
+    const size_t n = (size_t)ctx->n_slots;
+    if (n == 0) return EMC_OK;
+    if (!ctx->skey) {
+        Real *a, *b, *c, *g;
+        CK(dalloc(ctx, &a, n));
+        CK(dalloc(ctx, &b, n));
+        CK(dalloc(ctx, &c, n));
+        CK(dalloc(ctx, &g, n));
+        ctx->akx = a; ctx->aky = b; ctx->akz = c; ctx->atr = g;
+        if (nw) {
+            Real *d, *e, *f;
+            CK(dalloc(ctx, &d, n));
+            CK(dalloc(ctx, &e, n));
+            CK(dalloc(ctx, &f, n));
+            ctx->ax = d; ctx->ay = e; ctx->az = f;
+        }
+        CK(dalloc(ctx, &ctx->atag, n));
+        CK(dalloc(ctx, &ctx->aid, n));
+        CK(dalloc(ctx, &ctx->actr, n));
+        CK(dalloc(ctx, &ctx->skey, n));
+        ctx->n_keys = (int64_t)ctx->n_ens * (NV + 1) * ctx->ncell;
+        if (ctx->n_keys > 2048LL * 2048LL) return fail(ctx, EMC_EINVAL, "too many sort keys (ensembles x 4 x cells > 4M)");
+        CK(dalloc(ctx, &ctx->shist, (size_t)ctx->n_keys * 2));
+        CK(dalloc(ctx, &ctx->soffs, (size_t)ctx->n_keys));
+        CK(dalloc(ctx, &ctx->sblk, (size_t)((ctx->n_keys + 2047) / 2048)));
+    }
+    unsigned int* hist = ctx->shist;
+    unsigned int* cursor = ctx->shist + ctx->n_keys;
+    CK(cudaMemsetAsync(ctx->shist, 0, sizeof(unsigned int) * 2 * (size_t)ctx->n_keys, ctx->st));
+    DevParams alt = ctx->P;
+    alt.kx = ctx->akx; alt.ky = ctx->aky; alt.kz = ctx->akz;
+    alt.x = ctx->ax; alt.y = ctx->ay; alt.z = ctx->az; alt.tr = ctx->atr;
+    alt.tag = ctx->atag; alt.id = ctx->aid; alt.ctr = ctx->actr;
+    launch_sort<Real>(ctx->P, alt, nw, ctx->skey, hist, nullptr, nullptr, 0, ctx->st);
+    const int64_t nb = (ctx->n_keys + 2047) / 2048;
+    k_scan_blocks<<<(unsigned)nb, 1024, 0, ctx->st>>>(hist, ctx->soffs, ctx->sblk, ctx->n_keys);
+    if (nb > 1) {
+        unsigned int* tmp = cursor;  // cursor is zero; borrow it for the block totals' scan
+        k_scan_blocks<<<1, 1024, 0, ctx->st>>>(ctx->sblk, tmp, tmp + nb, nb);
+        CK(cudaMemcpyAsync(ctx->sblk, tmp, sizeof(unsigned int) * nb, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemsetAsync(cursor, 0, sizeof(unsigned int) * (size_t)ctx->n_keys, ctx->st));
+        k_scan_add<<<grid_for(ctx->n_keys, 256), 256, 0, ctx->st>>>(ctx->soffs, ctx->sblk, ctx->n_keys);
+    }
+    launch_sort<Real>(ctx->P, alt, nw, ctx->skey, nullptr, ctx->soffs, cursor, 1, ctx->st);
+    const size_t es = sizeof(Real);
+    CK(cudaMemcpyAsync(ctx->kx, ctx->akx, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->ky, ctx->aky, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->kz, ctx->akz, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->tr, ctx->atr, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+    if (nw) {
+        CK(cudaMemcpyAsync(ctx->x, ctx->ax, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(ctx->y, ctx->ay, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemcpyAsync(ctx->z, ctx->az, es * n, cudaMemcpyDeviceToDevice, ctx->st));
+    }
+    CK(cudaMemcpyAsync(ctx->tag, ctx->atag, 4 * n, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->id, ctx->aid, 4 * n, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->ctr, ctx->actr, 8 * n, cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->launches += 2 + (nb > 1 ? 3 : 1);
+    ctx->sorts += 1;
+    CK(cudaGetLastError());
+    return EMC_OK;
 }
 
 emc_status check_err(emc_ctx* ctx)
@@ -716,6 +865,36 @@ emc_status init_impl(emc_ctx* ctx)
     return check_err(ctx);
 }
 
+// Contact refill, Poisson update and field after a chunk: captured once into
+// a CUDA graph (fixed pointers and sizes) and replayed.
+template <typename Real>
+emc_status chunk_tail(emc_ctx* ctx)
+{
+    if (!ctx->use_graph) {
+        launch_inject<Real>(ctx->P, ctx->st);
+        ctx->launches += 1;
+        return poisson_update<Real>(ctx);
+    }
+    if (!ctx->g_tail_exec) {
+        const int64_t l0 = ctx->launches;
+        CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+        launch_inject<Real>(ctx->P, ctx->st);
+        ctx->launches += 1;
+        emc_status s = poisson_update<Real>(ctx);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+        if (s != EMC_OK) return s;
+        CK(e);
+        ctx->g_tail = g;
+        CK(cudaGraphInstantiate(&ctx->g_tail_exec, g, 0));
+        ctx->g_tail_launches = ctx->launches - l0;
+        ctx->launches = l0;
+    }
+    CK(cudaGraphLaunch(ctx->g_tail_exec, ctx->st));
+    ctx->launches += ctx->g_tail_launches;
+    return EMC_OK;
+}
+
 emc_status prof_pair(emc_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b)
 {
     while (ctx->ev_pool.size() < ctx->ev_used + 2) {
@@ -755,14 +934,17 @@ emc_status step_impl(emc_ctx* ctx, int32_t n)
         ctx->launches += 1;
         if (ctx->prof) CK(cudaEventRecord(e1, ctx->st));
         if (boundary) {
-            launch_inject<Real>(ctx->P, ctx->st);
-            ctx->launches += 1;
-            emc_status s = poisson_update<Real>(ctx);
+            emc_status s = chunk_tail<Real>(ctx);
             if (s != EMC_OK) return s;
         }
         CK(cudaGetLastError());
         ctx->steps_done += chunk;
         n -= chunk;
+        if (ctx->sort_period > 0 && ++ctx->flights_since_sort >= ctx->sort_period && (!nw || boundary)) {
+            emc_status s = sort_particles<Real>(ctx);
+            if (s != EMC_OK) return s;
+            ctx->flights_since_sort = 0;
+        }
     }
     return EMC_OK;
 }
@@ -784,6 +966,7 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
         return s;
     }
     ctx->st = static_cast<cudaStream_t>(stream);
+    ctx->use_graph = ctx->st != nullptr;  // the legacy default stream cannot be captured
     ctx->cfg.assign(cfgs, cfgs + n_ens);
     const emc_config& c0 = cfgs[0];
     ctx->n_ens = n_ens;
@@ -1021,7 +1204,9 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
     CK(cudaMallocAsync(&rhs, 8 * n, ctx->st));
     CK(cudaMallocAsync(&phi, 8 * n, ctx->st));
     CK(cudaMallocAsync(&bias, 8 * 3, ctx->st));
-    CK(cudaMallocAsync(&r32, 4 * n, ctx->st));
+    float* part = nullptr;
+    CK(cudaMallocAsync(&r32, 4 * (size_t)n, ctx->st));
+    CK(cudaMallocAsync(&part, 4 * (size_t)sweep_slices(n) * n, ctx->st));
     CK(cudaMemsetAsync(phi, 0, 8 * n, ctx->st));
     CK(cudaMemcpyAsync(bias, bc_volts, 24, cudaMemcpyHostToDevice, ctx->st));
     PoisGeo G = pgeo(ctx);
@@ -1036,9 +1221,9 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
     }
     for (int s = 0; s < kPoissonSweeps + 1; ++s) {
         k_resid<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, rhs, phi, r32);
-        k_sweep<<<dim3(grid_for(n, 16), 1), 256, 0, ctx->st>>>(ctx->G32, r32, phi, n, 1);
+        launch_sweep(ctx->G32, r32, part, phi, n, 1, ctx->st);
     }
-    ctx->launches += 1 + 2 * (kPoissonSweeps + 1);
+    ctx->launches += 1 + 3 * (kPoissonSweeps + 1);
     CK(cudaGetLastError());
     if (phi_out) CK(cudaMemcpyAsync(phi_out, phi, 8 * n, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaFreeAsync(rho, ctx->st));
@@ -1046,6 +1231,7 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
     CK(cudaFreeAsync(phi, ctx->st));
     CK(cudaFreeAsync(bias, ctx->st));
     CK(cudaFreeAsync(r32, ctx->st));
+    CK(cudaFreeAsync(part, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
 }
@@ -1059,7 +1245,9 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
 // library is loaded on each device that uses it.
 namespace {
 constexpr int kStaticCells = 8192;
-constexpr size_t kStaticDoubles = 3 * (size_t)kStaticCells + 4 + kStaticCells / 2;
+constexpr int kStaticSlices = (kStaticCells + 191) / 192;
+constexpr size_t kStaticDoubles = 3 * (size_t)kStaticCells + 4 + kStaticCells / 2 +
+                                  (size_t)kStaticSlices * kStaticCells / 2;
 static __device__ __align__(256) double g_poisson_scratch[kStaticDoubles];
 
 // device address of the scratch array, looked up once per device with that
@@ -1106,6 +1294,7 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, 
     double* rho = base + 2 * (size_t)kStaticCells;
     double* bias = base + 3 * (size_t)kStaticCells;
     float* r32 = reinterpret_cast<float*>(base + 3 * (size_t)kStaticCells + 4);
+    float* part = r32 + kStaticCells;
     // the previous call's contents are still there: start the potential at zero
     CK(cudaMemsetAsync(phi, 0, 8 * (size_t)n, ctx->st));
     CK(cudaMemcpyAsync(bias, bc_volts, 24, cudaMemcpyHostToDevice, ctx->st));
@@ -1121,9 +1310,9 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, 
     }
     for (int sw = 0; sw < kPoissonSweeps + 2; ++sw) {
         k_resid<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, rhs, phi, r32);
-        k_sweep<<<dim3(grid_for(n, 16), 1), 256, 0, ctx->st>>>(ctx->G32, r32, phi, n, 1);
+        launch_sweep(ctx->G32, r32, part, phi, n, 1, ctx->st);
     }
-    ctx->launches += 1 + 2 * (kPoissonSweeps + 2);
+    ctx->launches += 1 + 3 * (kPoissonSweeps + 2);
     CK(cudaGetLastError());
     if (phi_out_or_null)
         CK(cudaMemcpyAsync(phi_out_or_null, phi, 8 * (size_t)n, cudaMemcpyDeviceToHost, ctx->st));
@@ -1265,6 +1454,8 @@ void emc_destroy(emc_ctx* ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->st);
+    if (ctx->g_tail_exec) cudaGraphExecDestroy(ctx->g_tail_exec);
+    if (ctx->g_tail) cudaGraphDestroy(ctx->g_tail);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;

@@ -8,4 +8,6 @@ template void launch_inject<float>(const DevParams&, cudaStream_t);
 template cudaError_t flight_set_smem<float>(size_t);
 template size_t flight_smem_bytes<float>(int, int);
 template int flight_blocks_per_sm<float>(bool, int, size_t);
+template void launch_sort<float>(const DevParams&, const DevParams&, bool, uint32_t*, unsigned int*, const unsigned int*,
+                                unsigned int*, int, cudaStream_t);
 }  // namespace emc

@@ -8,4 +8,6 @@ template void launch_inject<double>(const DevParams&, cudaStream_t);
 template cudaError_t flight_set_smem<double>(size_t);
 template size_t flight_smem_bytes<double>(int, int);
 template int flight_blocks_per_sm<double>(bool, int, size_t);
+template void launch_sort<double>(const DevParams&, const DevParams&, bool, uint32_t*, unsigned int*, const unsigned int*,
+                                unsigned int*, int, cudaStream_t);
 }  // namespace emc

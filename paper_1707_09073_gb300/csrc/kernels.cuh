@@ -110,6 +110,30 @@ __device__ __forceinline__ void tally_cnt(BlockTally* bt, const DevParams& P, in
     }
 }
 
+// Atomic add of d to base[key] from the lanes currently executing together:
+// lanes with the same key (particles of one subcell after sorting) combine
+// their contributions and one of them issues the atomic.
+__device__ __forceinline__ void agg_add_ll(long long* base, int key, long long d)
+{
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    const int leader = __ffs(peers) - 1;
+    long long sum = d;
+    if (peers != (1u << leader)) {
+        // gather the peers' contributions, lowest lane first
+        sum = 0;
+        for (unsigned m = peers; m; m &= m - 1u) sum += __shfl_sync(peers, d, __ffs(m) - 1);
+    }
+    if ((threadIdx.x & 31) == leader && sum != 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(base + key), (unsigned long long)sum);
+}
+
+__device__ __forceinline__ void agg_add_i(int* base, int key)
+{
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, key);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(base + key, __popc(peers));
+}
+
 // ------------------------------------------------------------ particle
 template <typename Real>
 struct Part {
@@ -460,8 +484,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
         const int c = cell_of<Real>(K, q.x, q.y, q.z);
         // net emission: mech 1 absorbs, 2 emits; 4+2j absorbs, 5+2j emits
         const long long d = (mech == 1) ? -1 : (mech == 2 ? 1 : ((mech & 1) ? 1 : -1));
-        atomicAdd(reinterpret_cast<unsigned long long*>(&P.heat[((size_t)q.e * K.ncell + c) * 2 + (mech <= 2 ? 0 : 1)]),
-                  (unsigned long long)d);
+        agg_add_ll(P.heat, (q.e * K.ncell + c) * 2 + (mech <= 2 ? 0 : 1), d);
     }
     q.v = j;
     q.tr = Mth<Real>::neglog_u(Q.u1) * ph.inv_g0[j];
@@ -499,15 +522,41 @@ struct Samples {
 };
 
 // -------------------------------------------------------------- flight
-// Persistent blocks; block b owns the slot range [b * per_block,
-// (b + 1) * per_block) and walks it one blockDim tile at a time (coalesced
-// state loads and stores); each thread advances its particle by n_steps time
-// steps.  Inside a step every iteration carries the particle to its next
-// event -- the end of the step or a scattering -- through one shared drift
-// and wall check, so the warp runs the drift once per iteration whatever
-// event each lane meets.  The rate table of a single table set is staged in
-// shared memory for bins [0, nbs); the per-table-set physics for up to 64
-// table sets.
+// Persistent blocks, no block-level barriers after set-up: warp g of the
+// grid advances the 32-slot chunks g, g + W, g + 2W, ... (W warps in the
+// grid), one particle per lane, with coalesced state loads and stores.  The
+// round robin spreads every stretch of the slot range over all warps, so a
+// sorted range (neighbouring slots in neighbouring subcells, a hot drain end
+// and a cool source end) still balances.  Inside a step every iteration
+// carries the particle to its next event -- the end of the step or a
+// scattering -- through one shared drift and wall check.  Block tallies in
+// shared memory are indexed by ensemble (the first WE ensembles; others go
+// straight to global atomics).  The rate table of a single table set is
+// staged in shared memory for bins [0, nbs); the per-table-set physics for
+// up to 64 table sets.
+__device__ __forceinline__ void flush_window(const DevParams& P, BlockTally* bt)
+{
+    for (int i = threadIdx.x; i < WE * NV * NM; i += blockDim.x) {
+        const int w = i / (NV * NM), j = i - w * NV * NM;
+        const unsigned int n = bt->ev[w][j];
+        if (n && w < P.n_ens) atomicAdd(&P.events[(size_t)w * NV * NM + j], (unsigned long long)n);
+    }
+    for (int i = threadIdx.x; i < WE * NCNT; i += blockDim.x) {
+        const int w = i / NCNT, j = i - w * NCNT;
+        const unsigned int n = bt->cnt[w][j];
+        if (n && w < P.n_ens) {
+            atomicAdd(&P.cnt[(size_t)w * NCNT + j], (unsigned long long)n);
+            if (j == CNT_SRC_OUT || j == CNT_DRN_OUT)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&P.alive[w]), (unsigned long long)(-(long long)n));
+        }
+    }
+    for (int i = threadIdx.x; i < WE * NSUM; i += blockDim.x) {
+        const int w = i / NSUM, j = i - w * NSUM;
+        const double x = bt->sums[w][j];
+        if (x != 0.0 && w < P.n_ens) atomicAdd(&P.sums[(size_t)w * NSUM + j], x);
+    }
+}
+
 template <typename Real, bool NW>
 __global__ void __launch_bounds__(256, 3)
     k_flight(const DevParams P, const KConst<Real> K, int n_steps, int count_charge)
@@ -530,15 +579,18 @@ __global__ void __launch_bounds__(256, 3)
         reinterpret_cast<Real*>(ph_s)[i] = reinterpret_cast<const Real*>(ph_g)[i];
     for (int i = threadIdx.x; i < (int)(sizeof(BlockTally) / 4); i += blockDim.x)
         reinterpret_cast<unsigned int*>(bt)[i] = 0u;
-    const int64_t b0 = (int64_t)blockIdx.x * K.per_block;
-    const int64_t b1 = min(b0 + K.per_block, P.n_slots);
-    const int e_base = b0 < P.n_slots ? int(P.tag[b0] >> 8) : 0;
     __syncthreads();
 
     const Real dt = K.dt;
     const int nbs1 = (K.n_tab == 1) ? nbs : 0;
+    const int e_base = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t n_chunks = (P.n_slots + 31) >> 5;
     Samples<Real> S;
-    for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) {
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+        const int64_t p = c * 32 + lane;
+        if (p >= P.n_slots) continue;
         const uint32_t tg = P.tag[p];
         if ((tg & 0xFFu) == DEAD) continue;
         QEntry<Real> Q;
@@ -606,31 +658,11 @@ __global__ void __launch_bounds__(256, 3)
         }
         store<Real>(P, p, q, NW);
         P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
-        if (NW && count_charge && live)
-            atomicAdd(&P.charge[(size_t)q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z)], 1);
+        if (NW && count_charge && live) agg_add_i(P.charge, q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z));
     }
     S.flush(P, bt, e_base);
     __syncthreads();
-    for (int i = threadIdx.x; i < WE * NV * NM; i += blockDim.x) {
-        const int w = i / (NV * NM), j = i - w * NV * NM;
-        const unsigned int n = bt->ev[w][j];
-        if (n && e_base + w < P.n_ens) atomicAdd(&P.events[(size_t)(e_base + w) * NV * NM + j], (unsigned long long)n);
-    }
-    for (int i = threadIdx.x; i < WE * NCNT; i += blockDim.x) {
-        const int w = i / NCNT, j = i - w * NCNT;
-        const unsigned int n = bt->cnt[w][j];
-        if (n && e_base + w < P.n_ens) {
-            atomicAdd(&P.cnt[(size_t)(e_base + w) * NCNT + j], (unsigned long long)n);
-            if (j == CNT_SRC_OUT || j == CNT_DRN_OUT)
-                atomicAdd(reinterpret_cast<unsigned long long*>(&P.alive[e_base + w]),
-                          (unsigned long long)(-(long long)n));
-        }
-    }
-    for (int i = threadIdx.x; i < WE * NSUM; i += blockDim.x) {
-        const int w = i / NSUM, j = i - w * NSUM;
-        const double x = bt->sums[w][j];
-        if (x != 0.0 && e_base + w < P.n_ens) atomicAdd(&P.sums[(size_t)(e_base + w) * NSUM + j], x);
-    }
+    flush_window(P, bt);
 }
 
 // ---------------------------------------------------------------- init
@@ -789,6 +821,61 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
     }
 }
 
+// ----------------------------------------------------------------- sort
+// Counting sort of the particle slots by key (ensemble, valley, subcell),
+// free slots (valley DEAD) last within each ensemble's range, so that the
+// ranges stay where they are.  Key pass: histogram; the host-side scan gives
+// the offsets; scatter pass: every slot moves to offset[key] + rank (the rank
+// order inside a key does not matter: every particle carries its own id and
+// Philox stream).
+template <typename Real, bool NW>
+__global__ void k_sort_keys(const DevParams P, const KConst<Real> K, uint32_t* key, unsigned int* hist)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_slots) return;
+    const uint32_t tg = P.tag[p];
+    const int e = int(tg >> 8);
+    const int v = (tg & 0xFFu) == DEAD ? NV : int(tg & 0xFFu);
+    int c = 0;
+    if (NW && v < NV)
+        c = cell_of<Real>(K, static_cast<const Real*>(P.x)[p], static_cast<const Real*>(P.y)[p],
+                          static_cast<const Real*>(P.z)[p]);
+    const uint32_t kk = (uint32_t)(((size_t)e * (NV + 1) + v) * K.ncell + c);
+    key[p] = kk;
+    const unsigned peers = __match_any_sync(__activemask(), kk);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[kk], (unsigned)__popc(peers));
+}
+
+template <typename Real, bool NW>
+__global__ void k_sort_scatter(const DevParams P, const uint32_t* key, const unsigned int* offs,
+                               unsigned int* cursor, DevParams Q)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n_slots) return;
+    const uint32_t kk = key[p];
+    // one cursor claim per group of lanes with the same key
+    const unsigned peers = __match_any_sync(__activemask(), kk);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[kk], (unsigned)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int64_t d = (int64_t)offs[kk] + base + __popc(peers & ((1u << lane) - 1u));
+    static_cast<Real*>(Q.kx)[d] = static_cast<const Real*>(P.kx)[p];
+    static_cast<Real*>(Q.ky)[d] = static_cast<const Real*>(P.ky)[p];
+    static_cast<Real*>(Q.kz)[d] = static_cast<const Real*>(P.kz)[p];
+    if (NW) {
+        static_cast<Real*>(Q.x)[d] = static_cast<const Real*>(P.x)[p];
+        static_cast<Real*>(Q.y)[d] = static_cast<const Real*>(P.y)[p];
+        static_cast<Real*>(Q.z)[d] = static_cast<const Real*>(P.z)[p];
+    }
+    static_cast<Real*>(Q.tr)[d] = static_cast<const Real*>(P.tr)[p];
+    Q.ctr[d] = P.ctr[p];
+    Q.tag[d] = P.tag[p];
+    const uint32_t id = P.id[p];
+    Q.id[d] = id;
+    P.slot_of_id[P.ens_off[P.tag[p] >> 8] + id] = uint32_t(d);
+}
+
 // --------------------------------------------------------------- launch
 template <typename Real>
 size_t flight_smem_bytes(int nb_smem, int n_tab_s)
@@ -841,15 +928,37 @@ void launch_flight(const DevParams& P, bool nw, int n_steps, int count_charge, i
     K.n_tab = P.n_tab;
     K.n_tab_s = P.n_tab <= 64 ? P.n_tab : 0;
     const int64_t tiles = (P.n_slots + block - 1) / block;
-    const int64_t grid = tiles < grid_cap ? tiles : grid_cap;
-    K.per_block = ((P.n_slots + grid - 1) / grid + 31) / 32 * 32;
-    const int64_t g = (P.n_slots + K.per_block - 1) / K.per_block;
+    const int64_t g = tiles < grid_cap ? tiles : grid_cap;
+    K.per_block = 0;
     const size_t smem = flight_smem_bytes<Real>(K.nbs, K.n_tab_s);
     if (nw)
         k_flight<Real, true><<<(unsigned)g, block, smem, st>>>(P, K, n_steps, count_charge);
     else
         k_flight<Real, false><<<(unsigned)g, block, smem, st>>>(P, K, n_steps, count_charge);
 }
+template <typename Real>
+void launch_sort(const DevParams& P, const DevParams& alt, bool nw, uint32_t* key, unsigned int* hist,
+                 const unsigned int* offs, unsigned int* cursor, int phase, cudaStream_t st)
+{
+    if (P.n_slots <= 0) return;
+    KConst<Real> K{};
+    K.inv_dx = Real(1.0 / P.dx);
+    K.inv_dy = Real(1.0 / P.dy);
+    K.inv_dz = Real(1.0 / P.dz);
+    K.nx = P.nx;
+    K.ny = P.ny;
+    K.nz = P.nz;
+    K.ncell = P.ncell;
+    const unsigned grid = (unsigned)((P.n_slots + 255) / 256);
+    if (phase == 0) {
+        if (nw) k_sort_keys<Real, true><<<grid, 256, 0, st>>>(P, K, key, hist);
+        else k_sort_keys<Real, false><<<grid, 256, 0, st>>>(P, K, key, hist);
+    } else {
+        if (nw) k_sort_scatter<Real, true><<<grid, 256, 0, st>>>(P, key, offs, cursor, alt);
+        else k_sort_scatter<Real, false><<<grid, 256, 0, st>>>(P, key, offs, cursor, alt);
+    }
+}
+
 template <typename Real>
 void launch_init(const DevParams& P, bool nw, cudaStream_t st)
 {

@@ -148,3 +148,102 @@ def test_bulk_fp32_statistics(emc, oracle_mod):
         g, o = np.array(g), np.array(o)
         sig = np.sqrt(g.var(ddof=1) / len(g) + o.var(ddof=1) / len(o))
         assert abs(g.mean() - o.mean()) <= max(0.01 * abs(o.mean()), 3 * sig), (g.mean(), o.mean(), sig)
+
+
+@pytest.mark.parametrize("geom", ["bulk", "nanowire"])
+def test_sorted_fp64_bit_exact(emc, oracle_mod, geom):
+    """Sorting the particle slots every launch changes nothing: the FP64 build
+    still reproduces the oracle's integer tallies exactly."""
+    if geom == "bulk":
+        cfg = W.bulk(n_particles=5000, seed=5, steps_per_launch=10, sort_period=1)
+        steps = 60
+    else:
+        cfg = W.nanowire(n_particles=5000, nx=20, Lx=200e-9, Vd=3.0, seed=6, sort_period=1)
+        steps = 40
+    ref = oracle_mod.Sim(cfg)
+    ref.run(steps)
+    rt = ref.tallies()
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        g = gpu_tallies(emc, ctx)
+    assert np.array_equal(g["events"], rt["events"].sum(axis=0))
+    assert np.array_equal(g["obs"]["self_events"], rt["self_events"].astype(np.int64))
+    assert np.array_equal(g["obs"]["valley_steps"], rt["valley_steps"])
+    if geom == "nanowire":
+        assert np.array_equal(g["heat"], oracle_heat(rt["events"]))
+        assert np.array_equal(g["crossings"], rt["crossings"])
+        assert np.array_equal(g["charge"], rt["charge"])
+
+
+def test_sorted_fp32_same_integer_tallies(emc):
+    """FP32 production build: each particle's arithmetic does not depend on
+    its slot, so sorted and unsorted runs give identical integer tallies."""
+    base = W.nanowire(n_particles=20_000, nx=30, Lx=300e-9, Vd=4.0, seed=8)
+    out = []
+    for sp in (0, 2):
+        with emc.Context(W.copy_config(base, sort_period=sp)) as ctx:
+            ctx.emc_step(50)
+            out.append(gpu_tallies(emc, ctx))
+    a, b = out
+    for k in ("events", "heat", "crossings", "charge"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["obs"]["self_events"], b["obs"]["self_events"])
+    assert a["obs"]["n_alive"] == b["obs"]["n_alive"]
+
+
+def test_batched_equals_separate(emc):
+    """Several ensembles in one context give the same integer tallies as each
+    ensemble in a context of its own."""
+    cfgs = [W.nanowire(n_particles=3000 + 500 * i, nx=10, Lx=100e-9, Vd=float(i), seed=20 + i) for i in range(3)]
+    with emc.Context(cfgs) as ctx:
+        ctx.emc_step(30)
+        ev = ctx.emc_tally(emc.TALLY_EVENTS)
+        heat = ctx.emc_tally(emc.TALLY_HEAT)
+        cr = ctx.emc_tally(emc.TALLY_CROSSINGS)
+    for i, c in enumerate(cfgs):
+        with emc.Context(c) as one:
+            one.emc_step(30)
+            assert np.array_equal(one.emc_tally(emc.TALLY_EVENTS)[0], ev[i])
+            assert np.array_equal(one.emc_tally(emc.TALLY_HEAT)[0], heat[i])
+            assert np.array_equal(one.emc_tally(emc.TALLY_CROSSINGS)[0], cr[i])
+
+
+def test_edge_cases(emc):
+    # empty ensemble
+    with emc.Context(W.bulk(n_particles=0)) as ctx:
+        ctx.emc_step(5)
+        ob = ctx.emc_tally(emc.TALLY_OBS)[0]
+        assert ob["n_samples"] == 0 and ob["n_alive"] == 0
+        assert ctx.emc_tally(emc.TALLY_EVENTS).sum() == 0
+    # zero steps is a no-op, negative is rejected
+    with emc.Context(W.bulk(n_particles=33)) as ctx:
+        ctx.emc_step(0)
+        with pytest.raises(emc.EmcError):
+            ctx.emc_step(-1)
+        assert ctx.emc_tally(emc.TALLY_OBS)[0]["n_alive"] == 33
+    # invalid configurations
+    with pytest.raises(emc.EmcError):
+        emc.Context(W.bulk(n_particles=10, T=-1.0))
+    with pytest.raises(emc.EmcError):
+        emc.Context(W.bulk(n_particles=10, capacity=5))
+    with pytest.raises(emc.EmcError):
+        emc.Context([W.bulk(n_particles=10), W.nanowire(n_particles=10)])
+
+
+def test_graph_replay_same_as_direct(emc):
+    """On a non-default stream the per-chunk refill + Poisson tail is captured
+    once into a CUDA graph and replayed; the results must equal the direct
+    launches on the default stream."""
+    torch = pytest.importorskip("torch")
+    cfgs = [W.nanowire(n_particles=8000, nx=20, Lx=200e-9, Vd=float(v), seed=40 + v) for v in (1, 3)]
+    out = []
+    for use_stream in (False, True):
+        st = torch.cuda.Stream() if use_stream else None
+        with emc.Context(cfgs, stream=st.cuda_stream if st else None) as ctx:
+            ctx.emc_step(55)
+            out.append((ctx.emc_tally(emc.TALLY_EVENTS), ctx.emc_tally(emc.TALLY_HEAT),
+                        ctx.emc_tally(emc.TALLY_CHARGE), ctx.emc_tally(emc.TALLY_PHI)))
+            launches = ctx.launch_count()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    assert launches > 0

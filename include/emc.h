@@ -207,6 +207,54 @@ emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias);
 emc_status emc_profile(emc_ctx* ctx, int32_t enable);
 emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_launches);
 
+/* ------------------------------------------------------------------------
+ * Surrogate MLP (the learned part; the paper itself has no surrogate).
+ * A fully connected network n_in -> n_hidden (x n_layers, SiLU) -> n_out
+ * mapping local conditions to Monte Carlo observables, trained on data the
+ * Monte Carlo produces.  Products run on the tensor cores with BF16 operands
+ * and FP32 accumulation; master weights and Adam moments are FP32.  Inputs
+ * and outputs are normalised inside: x_n = (x - x_shift) / x_scale, the
+ * network predicts (y - y_shift) / y_scale.
+ * Parameter vector layout (emc_mlp_params): for each layer in order, W
+ * (out x in, row-major) then b (out).
+ */
+typedef struct emc_mlp emc_mlp;
+
+typedef struct emc_mlp_config {
+    int32_t n_in;        /* inputs, 1..16 */
+    int32_t n_hidden;    /* hidden width, multiple of 16, 16..256 */
+    int32_t n_layers;    /* hidden layers, 1..6 */
+    int32_t n_out;       /* outputs, 1..16 */
+    float x_shift[16], x_scale[16];
+    float y_shift[16], y_scale[16];
+    uint32_t seed;       /* weight initialisation (uniform +-sqrt(6 / fan_in)) */
+    int32_t pad_;
+} emc_mlp_config;
+
+typedef struct emc_train_config {
+    int64_t steps;       /* optimiser steps */
+    int32_t batch;       /* rows per step, sampled with replacement */
+    float lr, beta1, beta2, eps;  /* Adam */
+    uint32_t seed;       /* minibatch sampling stream */
+    int32_t pad_;
+} emc_train_config;
+
+emc_status emc_mlp_create(const emc_mlp_config* cfg, void* cuda_stream, emc_mlp** out);
+/* Train on the n rows of host arrays X [n][n_in], Y [n][n_out] (mean squared
+ * error of the normalised outputs).  loss_history: host float[steps] or NULL. */
+emc_status emc_mlp_train(emc_mlp* m, const float* X, const float* Y, int64_t n, const emc_train_config* tc,
+                         float* loss_history);
+/* Y [n][n_out] = network(X [n][n_in]); host arrays. */
+emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n);
+/* Loss and gradient of the loss w.r.t. the parameter vector on host rows
+ * X, Y (no update).  grad: host float[count] (see emc_mlp_params). */
+emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, float* grad, float* loss);
+/* Parameter vector: *count receives its length; get (dst != NULL) and/or
+ * set (src != NULL, applied after the get). */
+emc_status emc_mlp_params(emc_mlp* m, float* dst, const float* src, int64_t* count);
+const char* emc_mlp_last_error(const emc_mlp* m);
+void emc_mlp_destroy(emc_mlp* m);
+
 /* Diagnostics used by the test-suite. */
 /* Philox4x32-10 evaluated on the device for n (counter, key) pairs:
  * ctr[n][4], key[n][2] in, out[n][4] out (host arrays). */

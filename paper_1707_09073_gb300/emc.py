@@ -272,3 +272,110 @@ def obs_dict(o: EmcObs) -> dict:
         "self_events": np.array(o.self_events[:], dtype=np.int64), "overflow": o.overflow,
         "steps_done": o.steps_done, "n_alive": o.n_alive, "inject_starved": o.inject_starved,
     }
+
+
+# ------------------------------------------------------------ surrogate MLP
+class EmcMlpConfig(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_layers", C.c_int32), ("n_out", C.c_int32),
+                ("x_shift", C.c_float * 16), ("x_scale", C.c_float * 16),
+                ("y_shift", C.c_float * 16), ("y_scale", C.c_float * 16),
+                ("seed", C.c_uint32), ("pad_", C.c_int32)]
+
+
+class EmcTrainConfig(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint32), ("pad_", C.c_int32)]
+
+
+def _mlp_lib():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        P, I64 = C.c_void_p, C.c_int64
+        fp = C.POINTER(C.c_float)
+        L.emc_mlp_create.argtypes = [C.POINTER(EmcMlpConfig), P, C.POINTER(P)]
+        L.emc_mlp_train.argtypes = [P, fp, fp, I64, C.POINTER(EmcTrainConfig), fp]
+        L.emc_mlp_infer.argtypes = [P, fp, fp, I64]
+        L.emc_mlp_grad.argtypes = [P, fp, fp, I64, fp, fp]
+        L.emc_mlp_params.argtypes = [P, fp, fp, C.POINTER(I64)]
+        L.emc_mlp_last_error.argtypes = [P]
+        L.emc_mlp_last_error.restype = C.c_char_p
+        L.emc_mlp_destroy.argtypes = [P]
+        for f in ("emc_mlp_create", "emc_mlp_train", "emc_mlp_infer", "emc_mlp_grad", "emc_mlp_params"):
+            getattr(L, f).restype = C.c_int
+        L._mlp_ready = True
+    return L
+
+
+class Mlp:
+    """The surrogate network of the C ABI (emc_mlp_*).  x_shift/x_scale and
+    y_shift/y_scale normalise inputs and outputs inside the library."""
+
+    def __init__(self, n_in, n_hidden, n_layers, n_out, x_shift, x_scale, y_shift, y_scale, seed=0, stream=None):
+        c = EmcMlpConfig()
+        c.n_in, c.n_hidden, c.n_layers, c.n_out, c.seed = n_in, n_hidden, n_layers, n_out, seed
+        for arr, vals in ((c.x_shift, x_shift), (c.x_scale, x_scale), (c.y_shift, y_shift), (c.y_scale, y_scale)):
+            for i, v in enumerate(vals):
+                arr[i] = float(v)
+        for i in range(n_in, 16):
+            c.x_scale[i] = 1.0
+        for i in range(n_out, 16):
+            c.y_scale[i] = 1.0
+        self.cfg = c
+        self.n_in, self.n_out = n_in, n_out
+        self.h = C.c_void_p()
+        st = _mlp_lib().emc_mlp_create(C.byref(c), C.c_void_p(stream or 0), C.byref(self.h))
+        if st != 0:
+            msg = _mlp_lib().emc_mlp_last_error(self.h).decode() if self.h else ""
+            self.close()
+            raise EmcError(st, msg)
+
+    def _check(self, st):
+        if st != 0:
+            raise EmcError(st, _mlp_lib().emc_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            _mlp_lib().emc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def train(self, X, Y, steps, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        t = EmcTrainConfig()
+        t.steps, t.batch, t.lr, t.beta1, t.beta2, t.eps, t.seed = steps, batch, lr, beta1, beta2, eps, seed
+        hist = np.zeros(max(steps, 1), dtype=np.float32)
+        self._check(_mlp_lib().emc_mlp_train(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0], C.byref(t),
+                                             _p(hist, C.c_float)))
+        return hist[:steps]
+
+    def infer(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], self.n_out), dtype=np.float32)
+        self._check(_mlp_lib().emc_mlp_infer(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0]))
+        return Y
+
+    def grad(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.zeros(self.n_params(), dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._check(_mlp_lib().emc_mlp_grad(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0],
+                                            _p(g, C.c_float), _p(loss, C.c_float)))
+        return float(loss[0]), g
+
+    def n_params(self) -> int:
+        n = C.c_int64()
+        self._check(_mlp_lib().emc_mlp_params(self.h, None, None, C.byref(n)))
+        return n.value
+
+    def params(self, new=None):
+        n = self.n_params()
+        out = np.zeros(n, dtype=np.float32)
+        src = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+        cnt = C.c_int64()
+        self._check(_mlp_lib().emc_mlp_params(self.h, _p(out, C.c_float), _p(src, C.c_float) if src is not None else None,
+                                              C.byref(cnt)))
+        return out

@@ -247,3 +247,28 @@ def test_graph_replay_same_as_direct(emc):
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
     assert launches > 0
+
+
+def test_heterogeneous_batch_fp64_bit_exact(emc, oracle_mod):
+    """40 bulk ensembles with different temperature, doping, field and size
+    in one context (40 table sets, ensembles beyond the shared-memory tally
+    slots): each reproduces its own oracle run exactly."""
+    rng = np.random.default_rng(4)
+    cfgs = []
+    for e in range(40):
+        cfgs.append(W.bulk(n_particles=int(10 ** rng.uniform(2, 3.2)), field_V_m=rng.uniform(0, 4e7),
+                           T=rng.uniform(300, 600), Nd_cm3=10 ** rng.uniform(16, 19), seed=100 + e,
+                           steps_per_launch=9))
+    steps = 30
+    with emc.Context(cfgs, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        ev = ctx.emc_tally(emc.TALLY_EVENTS)
+        obs = ctx.emc_tally(emc.TALLY_OBS)
+    for e in (0, 7, 31, 32, 33, 39):
+        ref = oracle_mod.Sim(cfgs[e])
+        ref.run(steps)
+        rt = ref.tallies()
+        assert np.array_equal(ev[e], rt["events"].sum(axis=0)), e
+        assert np.array_equal(obs[e]["self_events"], rt["self_events"].astype(np.int64)), e
+        assert np.array_equal(obs[e]["valley_steps"], rt["valley_steps"]), e
+        assert obs[e]["sum_E"] == pytest.approx(rt["sum_E"], rel=1e-10)

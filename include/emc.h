@@ -192,6 +192,20 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null,
 emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null,
                                     const double* bc_volts, double* phi_out_or_null);
 
+/* Lattice temperature per subcell of ensemble ens (nanowire contexts whose
+ * ensembles share one material and doping): T_cells[n] in K, n = the
+ * subcell count (or 1 for a uniform value).  The phonon feedback of the
+ * thermal side on the electrons (the paragraph opening "the phonon MC
+ * simulations and Fourier's law analysis are then carried out").  Rates
+ * are tabulated on temperature bins T_k = 250 K + 5 K k (k = 0..150) and a
+ * subcell uses the bin nearest its temperature; a scattering is tried
+ * against the ensemble's Gamma0 (the largest total rate over the bins in
+ * use) with the table of the particle's current subcell, so self-scattering
+ * stays exact across subcells.  Residual flight times are rescaled by
+ * Gamma0_old / Gamma0_new.  Contact refills draw thermal electrons at the
+ * contact subcell's temperature.  The first call builds the 151 bin tables. */
+emc_status emc_set_temperature(emc_ctx* ctx, int32_t ens, const double* T_cells, int32_t n);
+
 /* Set the terminal voltages of ensemble ens and re-solve its field. */
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg);
 

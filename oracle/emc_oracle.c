@@ -50,6 +50,13 @@ struct orc_sim {
     int64_t *charge;  /* [ncell] */
     double *phi, *Ef; /* [ncell], [ncell][3] */
     orc_tallies t;
+    /* per-subcell temperature: bins T_k = 250 + 5 k K, k = 0..150 */
+    int tmode;
+    double *btab;            /* [NTB][NV][NB][NM] cumulative / Gamma0 of the bin */
+    double bg0[151][ORC_NV]; /* Gamma0 of each bin */
+    double bbeta2[151], bkT[151];
+    double g0e[ORC_NV];      /* Gamma0 of the ensemble (maximum over the bins in use) */
+    int *cbin;               /* [ncell] */
 };
 
 /* ---------------------------------------------------------------- Philox */
@@ -174,6 +181,15 @@ double orc_rate(const orc_sim* s, int v, int mech, double E)
                (sqrt(2.0) * PI_D * s->c.rho * pow(HBAR, 3) * wiv);
     }
     return 0.0;
+}
+
+/* temperature-dependent constants of the rates */
+static void set_temperature_consts(orc_sim* s, double T)
+{
+    s->kT = K_B * T;
+    s->beta2 = Q_E * Q_E * s->c.Nd / (s->c.eps_s * EPS_0 * s->kT);
+    s->N_lo = 1.0 / (exp(s->hw_lo / s->kT) - 1.0);
+    s->N_iv = 1.0 / (exp(s->hw_iv / s->kT) - 1.0);
 }
 
 /* Tables at the lower edge of each bin; Gamma0 per valley is the maximum
@@ -307,7 +323,7 @@ static void new_electron(orc_sim* s, int64_t id, const double lo[3], const doubl
         s->x[id] = s->y[id] = s->z[id] = 0.0;
     }
     draw4(s, id, u);
-    s->tr[id] = -log(u[0]) / s->gamma0[0];
+    s->tr[id] = -log(u[0]) / (s->tmode ? s->g0e[0] : s->gamma0[0]);
     s->alive[id] = 1;
 }
 
@@ -436,8 +452,17 @@ static void scatter(orc_sim* s, int64_t p)
         b = (int)fb;
     }
     const double* C = s->table + ((size_t)v * s->nb + b) * ORC_NM;
+    double beta2 = s->beta2;
     int mech = -1;
-    if (s->c.exact_rates) {
+    if (s->tmode) {
+        /* the table of the particle's subcell temperature, tried against the
+         * ensemble's Gamma0 */
+        int k = s->cbin[cell_of(s, p)];
+        C = s->btab + (((size_t)k * ORC_NV + v) * s->nb + b) * ORC_NM;
+        u[0] = u[0] * (s->g0e[v] / s->bg0[k][v]);
+        beta2 = s->bbeta2[k];
+    }
+    if (s->c.exact_rates && !s->tmode) {
         double acc = 0.0;
         for (int m = 0; m < ORC_NM; ++m) {
             acc += orc_rate(s, v, m, E) / s->gamma0[v];
@@ -477,7 +502,7 @@ static void scatter(orc_sim* s, int64_t p)
                     n[1] = s->ky[p] / k;
                     n[2] = s->kz[p] / k;
                 }
-                double ct = (mech == 0) ? orc_cos_imp(k, s->beta2, u[2]) : orc_cos_pop(k, kp, u[2]);
+                double ct = (mech == 0) ? orc_cos_imp(k, beta2, u[2]) : orc_cos_pop(k, kp, u[2]);
                 orc_rotate(n, ct, ph, dir);
             } else {
                 double ct = 1.0 - 2.0 * u[2], st = sqrt(fmax(0.0, 1.0 - ct * ct));
@@ -494,7 +519,7 @@ static void scatter(orc_sim* s, int64_t p)
         }
     }
     if (mech < 0) s->t.self_events[v]++;
-    s->tr[p] = -log(u[1]) / s->gamma0[vn];
+    s->tr[p] = -log(u[1]) / (s->tmode ? s->g0e[vn] : s->gamma0[vn]);
 }
 
 /* ------------------------------------------------------------- Poisson */
@@ -648,7 +673,9 @@ static void inject(orc_sim* s)
                     }
                     double lo[3] = {ix * s->dx, j * s->dy, l * s->dz};
                     double len[3] = {s->dx, s->dy, s->dz};
+                    if (s->tmode) set_temperature_consts(s, 250.0 + 5.0 * s->cbin[cid]);
                     new_electron(s, next, lo, len);
+                    if (s->tmode) set_temperature_consts(s, s->c.T);
                     s->t.crossings[2 + side]++;
                     ++next;
                 }
@@ -731,10 +758,54 @@ void orc_destroy(orc_sim* s)
     free(s->x); free(s->y); free(s->z);
     free(s->tr); free(s->valley); free(s->alive); free(s->ctr);
     free(s->events); free(s->charge); free(s->phi); free(s->Ef);
+    free(s->btab); free(s->cbin);
     free(s);
 }
 
 int orc_ncell(const orc_sim* s) { return s->ncell; }
+
+/* Lattice temperature per subcell (n = subcell count, or 1): bins of 5 K
+ * from 250 K, nearest bin per subcell; the ensemble's Gamma0 is the largest
+ * total rate over the bins in use and residual flights are rescaled by
+ * Gamma0_old / Gamma0_new. */
+void orc_set_temperature(orc_sim* s, const double* T, int n)
+{
+    const int NTB = 151;
+    if (!s->tmode) {
+        s->btab = malloc(sizeof(double) * NTB * ORC_NV * (size_t)s->nb * ORC_NM);
+        double* keep = s->table;
+        double keepg[ORC_NV];
+        memcpy(keepg, s->gamma0, sizeof keepg);
+        for (int k = 0; k < NTB; ++k) {
+            set_temperature_consts(s, 250.0 + 5.0 * k);
+            s->table = s->btab + (size_t)k * ORC_NV * s->nb * ORC_NM;
+            build_tables(s);
+            memcpy(s->bg0[k], s->gamma0, sizeof s->bg0[k]);
+            s->bbeta2[k] = s->beta2;
+            s->bkT[k] = s->kT;
+        }
+        s->table = keep;
+        memcpy(s->gamma0, keepg, sizeof keepg);
+        set_temperature_consts(s, s->c.T);
+        s->cbin = malloc(sizeof(int) * s->ncell);
+        memcpy(s->g0e, s->gamma0, sizeof s->g0e);
+        s->tmode = 1;
+    }
+    for (int c = 0; c < s->ncell; ++c) {
+        double t = (n == 1) ? T[0] : T[c];
+        long k = lround((t - 250.0) / 5.0);
+        if (k < 0) k = 0;
+        if (k > NTB - 1) k = NTB - 1;
+        s->cbin[c] = (int)k;
+    }
+    double gnew[ORC_NV] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < s->ncell; ++c)
+        for (int v = 0; v < ORC_NV; ++v)
+            if (s->bg0[s->cbin[c]][v] > gnew[v]) gnew[v] = s->bg0[s->cbin[c]][v];
+    for (int64_t p = 0; p < s->cap; ++p)
+        if (s->alive[p]) s->tr[p] *= s->g0e[s->valley[p]] / gnew[s->valley[p]];
+    memcpy(s->g0e, gnew, sizeof gnew);
+}
 
 void orc_set_bias(orc_sim* s, double Vs, double Vd, double Vg)
 {

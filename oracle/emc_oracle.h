@@ -78,6 +78,7 @@ void orc_get_phi(const orc_sim* s, double* phi, double* Ef /* [ncell][3] */);
 void orc_get_particles(const orc_sim* s, double* k /* [cap][3] */, double* r /* [cap][3] */,
                        double* tr, int32_t* valley, uint8_t* alive, uint64_t* ctr);
 void orc_set_bias(orc_sim* s, double Vs, double Vd, double Vg);
+void orc_set_temperature(orc_sim* s, const double* T, int n);
 /* Kane-Maxwellian initial energy draw, exposed for distribution tests:
  * fills E[n] (J) from stream key (seed, id) starting at counter 0. */
 void orc_sample_initial_energy(const orc_sim* s, int64_t n, double* E);

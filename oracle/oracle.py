@@ -93,6 +93,7 @@ def lib():
         L.orc_get_particles.argtypes = [P, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
                                         C.POINTER(C.c_uint64)]
         L.orc_set_bias.argtypes = [P, C.c_double, C.c_double, C.c_double]
+        L.orc_set_temperature.argtypes = [P, dp, C.c_int]
         L.orc_sample_initial_energy.argtypes = [P, C.c_int64, dp]
         L.orc_cos_pop.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_cos_pop.restype = C.c_double
@@ -178,6 +179,10 @@ class Sim:
 
     def set_bias(self, Vs, Vd, Vg):
         lib().orc_set_bias(self.h, Vs, Vd, Vg)
+
+    def set_temperature(self, T_cells):
+        T = np.ascontiguousarray(np.atleast_1d(T_cells), dtype=np.float64)
+        lib().orc_set_temperature(self.h, _ptr(T), int(T.size))
 
     def tallies(self) -> dict:
         t = OrcTallies()

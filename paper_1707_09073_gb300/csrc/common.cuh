@@ -14,6 +14,9 @@ constexpr int NM = 10;  // mechanisms per valley (see include/emc.h)
 constexpr int WE = 32;  // ensembles with shared-memory block tallies (by index)
 constexpr uint32_t DEAD = 0xFFu;
 constexpr int MAX_FLIGHTS_PER_STEP = 1 << 16;
+// per-subcell lattice temperature: rates tabulated on bins T_k = 250 K + 5 K k
+constexpr double TBIN_LO = 250.0, TBIN_DT = 5.0;
+constexpr int NTBIN = 151;
 constexpr int MAX_INIT_TRIALS = 1000;
 
 // CODATA 2018 (SI)
@@ -83,6 +86,12 @@ struct DevParams {
     long long* heat;              // [E][C][2]
     int* charge;                  // [E][C]
     long long* alive;             // [E] live particles (never reset)
+    // per-subcell temperature (null cell_bin: one temperature per ensemble)
+    const int32_t* cell_bin;      // [E][C] temperature bin of each subcell
+    const void* bin_table;        // Real[NTBIN][NV][NB][NM], cumulative / Gamma0 of the bin
+    const void* bin_phys;         // Phys<Real>[NTBIN]
+    const void* ens_g0;           // Real[E][NV]: Gamma0 of the ensemble (1/fs)
+    const void* ens_ig0;          // Real[E][NV]: its inverse (fs)
     int* err;
 };
 

@@ -20,6 +20,7 @@ template <typename Real> void launch_inject(const DevParams&, cudaStream_t);
 template <typename Real> cudaError_t flight_set_smem(size_t);
 template <typename Real> size_t flight_smem_bytes(int, int);
 template <typename Real> int flight_blocks_per_sm(bool, int, size_t);
+template <typename Real> void launch_rescale(const DevParams&, int, int64_t, const double*, cudaStream_t);
 template <typename Real>
 void launch_sort(const DevParams&, const DevParams&, bool, uint32_t*, unsigned int*, const unsigned int*, unsigned int*,
                  int, cudaStream_t);
@@ -105,6 +106,13 @@ struct emc_ctx {
     int64_t n_keys = 0;
     int64_t flights_since_sort = 0;
     int64_t sorts = 0;
+    // per-subcell temperature (built on the first emc_set_temperature)
+    int32_t* cell_bin = nullptr;
+    void *bin_table = nullptr, *bin_phys = nullptr, *ens_g0 = nullptr, *ens_ig0 = nullptr;
+    double* bin_tab64 = nullptr;
+    std::vector<double> bin_g0;         // [NTBIN][NV] Gamma0 of each bin, 1/fs
+    std::vector<double> ens_g0_host;    // [E][NV] current Gamma0 of each ensemble
+    std::vector<int32_t> cell_bin_host; // [E][C]
     // graph of the per-chunk tail (refill + Poisson update + field)
     cudaGraph_t g_tail = nullptr;
     cudaGraphExec_t g_tail_exec = nullptr;
@@ -717,6 +725,11 @@ void fill_params(emc_ctx* ctx)
     P.dt = ctx->dt_fs;
     P.events = ctx->events; P.cnt = ctx->cnt; P.sums = ctx->sums; P.heat = ctx->heat; P.charge = ctx->charge;
     P.alive = ctx->alive;
+    P.cell_bin = ctx->cell_bin;
+    P.bin_table = ctx->bin_table;
+    P.bin_phys = ctx->bin_phys;
+    P.ens_g0 = ctx->ens_g0;
+    P.ens_ig0 = ctx->ens_ig0;
     P.err = ctx->d_err;
     const size_t row = (size_t)NV * NM * (ctx->prec == EMC_FP64 ? 8 : 4);
     const int kib = ctx->cfg[0].table_smem_kb > 0 ? ctx->cfg[0].table_smem_kb : kSmemTableKiB;
@@ -819,6 +832,117 @@ emc_status sort_particles(emc_ctx* ctx)
     ctx->launches += 2 + (nb > 1 ? 3 : 1);
     ctx->sorts += 1;
     CK(cudaGetLastError());
+    return EMC_OK;
+}
+
+int temp_bin(double T)
+{
+    const long k = std::lround((T - TBIN_LO) / TBIN_DT);
+    return (int)std::min<long>(NTBIN - 1, std::max<long>(0, k));
+}
+
+// rate tables of every temperature bin (the context's single table set)
+template <typename Real>
+emc_status build_bins(emc_ctx* ctx)
+{
+    const int nb = ctx->nb;
+    std::vector<RateConst> rc(NTBIN);
+    for (int k = 0; k < NTBIN; ++k) {
+        emc_config c = ctx->cfg[0];
+        c.T_K = TBIN_LO + TBIN_DT * k;
+        rc[k] = make_rc(c);
+    }
+    RateConst* d_rc = nullptr;
+    double* d_g0 = nullptr;
+    CK(cudaMallocAsync(&d_rc, sizeof(RateConst) * NTBIN, ctx->st));
+    CK(cudaMallocAsync(&d_g0, sizeof(double) * NTBIN * NV, ctx->st));
+    CK(cudaMemcpyAsync(d_rc, rc.data(), sizeof(RateConst) * NTBIN, cudaMemcpyHostToDevice, ctx->st));
+    const int64_t rows = (int64_t)NTBIN * NV * nb;
+    CK(dalloc(ctx, &ctx->bin_tab64, (size_t)rows * NM));
+    Real* tabR = nullptr;
+    CK(dalloc(ctx, &tabR, (size_t)rows * NM));
+    ctx->bin_table = tabR;
+    k_rates<<<grid_for(rows, 128), 128, 0, ctx->st>>>(d_rc, NTBIN, nb, ctx->dE, ctx->bin_tab64);
+    k_gamma0<<<NTBIN * NV, 256, 0, ctx->st>>>(ctx->bin_tab64, nb, d_g0);
+    k_normalise<Real><<<grid_for(rows * NM, 256), 256, 0, ctx->st>>>(ctx->bin_tab64, d_g0, nb, rows * NM, tabR);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    ctx->bin_g0.assign((size_t)NTBIN * NV, 0.0);
+    CK(cudaMemcpyAsync(ctx->bin_g0.data(), d_g0, sizeof(double) * NTBIN * NV, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaFreeAsync(d_rc, ctx->st));
+    CK(cudaFreeAsync(d_g0, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<Phys<Real>> ph(NTBIN);
+    for (int k = 0; k < NTBIN; ++k) {
+        emc_config c = ctx->cfg[0];
+        c.T_K = TBIN_LO + TBIN_DT * k;
+        ph[k] = make_phys<Real>(c, rc[k], &ctx->bin_g0[(size_t)k * NV]);
+    }
+    Phys<Real>* d_ph = nullptr;
+    CK(dalloc(ctx, &d_ph, NTBIN));
+    CK(cudaMemcpyAsync(d_ph, ph.data(), sizeof(Phys<Real>) * NTBIN, cudaMemcpyHostToDevice, ctx->st));
+    ctx->bin_phys = d_ph;
+    Real *g0 = nullptr, *ig0 = nullptr;
+    CK(dalloc(ctx, &g0, (size_t)ctx->n_ens * NV));
+    CK(dalloc(ctx, &ig0, (size_t)ctx->n_ens * NV));
+    ctx->ens_g0 = g0;
+    ctx->ens_ig0 = ig0;
+    CK(dalloc(ctx, &ctx->cell_bin, (size_t)ctx->n_ens * ctx->ncell));
+    // start every ensemble from its own uniform temperature and Gamma0
+    ctx->cell_bin_host.assign((size_t)ctx->n_ens * ctx->ncell, 0);
+    ctx->ens_g0_host.assign((size_t)ctx->n_ens * NV, 0.0);
+    for (int e = 0; e < ctx->n_ens; ++e) {
+        const int k = temp_bin(ctx->cfg[e].T_K);
+        for (int cc = 0; cc < ctx->ncell; ++cc) ctx->cell_bin_host[(size_t)e * ctx->ncell + cc] = k;
+        for (int v = 0; v < NV; ++v) ctx->ens_g0_host[(size_t)e * NV + v] = ctx->g0_host[(size_t)ctx->tabset[e] * NV + v];
+    }
+    return EMC_OK;
+}
+
+template <typename Real>
+emc_status set_temperature_impl(emc_ctx* ctx, int ens, const double* T, int n)
+{
+    emc_status s;
+    if (!ctx->cell_bin && (s = build_bins<Real>(ctx)) != EMC_OK) return s;
+    const int C = ctx->ncell;
+    int32_t* cb = &ctx->cell_bin_host[(size_t)ens * C];
+    for (int c = 0; c < C; ++c) cb[c] = temp_bin(n == 1 ? T[0] : T[c]);
+    // Gamma0 of the ensemble: the largest total rate over the bins it uses
+    double g_new[NV] = {0, 0, 0}, ratio[NV];
+    std::vector<char> used(NTBIN, 0);
+    for (int c = 0; c < C; ++c) used[cb[c]] = 1;
+    for (int k = 0; k < NTBIN; ++k)
+        if (used[k])
+            for (int v = 0; v < NV; ++v) g_new[v] = std::max(g_new[v], ctx->bin_g0[(size_t)k * NV + v]);
+    for (int v = 0; v < NV; ++v) {
+        ratio[v] = ctx->ens_g0_host[(size_t)ens * NV + v] / g_new[v];
+        ctx->ens_g0_host[(size_t)ens * NV + v] = g_new[v];
+    }
+    Real gR[NV], igR[NV];
+    for (int v = 0; v < NV; ++v) {
+        gR[v] = Real(g_new[v]);
+        igR[v] = Real(1.0 / g_new[v]);
+    }
+    CK(cudaMemcpyAsync(ctx->cell_bin + (size_t)ens * C, cb, sizeof(int32_t) * C, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(static_cast<Real*>(ctx->ens_g0) + (size_t)ens * NV, gR, sizeof gR, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(static_cast<Real*>(ctx->ens_ig0) + (size_t)ens * NV, igR, sizeof igR, cudaMemcpyHostToDevice,
+                       ctx->st));
+    double* d_ratio = nullptr;
+    CK(cudaMallocAsync(&d_ratio, sizeof ratio, ctx->st));
+    CK(cudaMemcpyAsync(d_ratio, ratio, sizeof ratio, cudaMemcpyHostToDevice, ctx->st));
+    fill_params(ctx);
+    launch_rescale<Real>(ctx->P, ens, ctx->cap[ens], d_ratio, ctx->st);
+    ctx->launches += 1;
+    CK(cudaFreeAsync(d_ratio, ctx->st));
+    CK(cudaGetLastError());
+    // the captured chunk tail holds the old kernel parameters
+    if (ctx->g_tail_exec) {
+        CK(cudaGraphExecDestroy(ctx->g_tail_exec));
+        CK(cudaGraphDestroy(ctx->g_tail));
+        ctx->g_tail_exec = nullptr;
+        ctx->g_tail = nullptr;
+    }
+    CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
 }
 
@@ -1364,6 +1488,18 @@ emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_lau
     if (flight_ms) *flight_ms = tot;
     if (flight_launches) *flight_launches = (int64_t)(ctx->ev_used / 2);
     return EMC_OK;
+}
+
+emc_status emc_set_temperature(emc_ctx* ctx, int32_t ens, const double* T_cells, int32_t n)
+{
+    if (!ctx || !T_cells || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
+    if (ctx->geom != EMC_GEOM_NANOWIRE || ctx->n_tab != 1)
+        return fail(ctx, EMC_ESTATE, "emc_set_temperature needs a nanowire context whose ensembles share one material/doping");
+    if (n != 1 && n != ctx->ncell) return fail(ctx, EMC_EINVAL, "emc_set_temperature: n must be 1 or the subcell count");
+    for (int i = 0; i < n; ++i)
+        if (!(T_cells[i] > 0.0)) return fail(ctx, EMC_EINVAL, "emc_set_temperature: temperatures must be positive");
+    return ctx->prec == EMC_FP64 ? set_temperature_impl<double>(ctx, ens, T_cells, n)
+                                 : set_temperature_impl<float>(ctx, ens, T_cells, n);
 }
 
 emc_status emc_debug_philox(emc_ctx* ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n)

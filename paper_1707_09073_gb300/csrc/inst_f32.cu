@@ -4,6 +4,7 @@
 namespace emc {
 template void launch_flight<float>(const DevParams&, bool, int, int, int, int, cudaStream_t);
 template void launch_init<float>(const DevParams&, bool, cudaStream_t);
+template void launch_rescale<float>(const DevParams&, int, int64_t, const double*, cudaStream_t);
 template void launch_inject<float>(const DevParams&, cudaStream_t);
 template cudaError_t flight_set_smem<float>(size_t);
 template size_t flight_smem_bytes<float>(int, int);

@@ -4,6 +4,7 @@
 namespace emc {
 template void launch_flight<double>(const DevParams&, bool, int, int, int, int, cudaStream_t);
 template void launch_init<double>(const DevParams&, bool, cudaStream_t);
+template void launch_rescale<double>(const DevParams&, int, int64_t, const double*, cudaStream_t);
 template void launch_inject<double>(const DevParams&, cudaStream_t);
 template cudaError_t flight_set_smem<double>(size_t);
 template size_t flight_smem_bytes<double>(int, int);

@@ -348,6 +348,8 @@ template <typename Real>
 struct QEntry {
     Part<Real> q;
     Real u1, u2, u3;
+    Real beta2;          // screening of the subcell's temperature
+    const Real* ig0;     // 1/Gamma0 per valley used for the next flight time
     int mech;
 };
 
@@ -359,12 +361,24 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
 {
     Part<Real>& q = Q.q;
     const U4 r = q.draw();
-    const Real u0 = u01<Real>(r.a);
+    Real u0 = u01<Real>(r.a);
     Q.u1 = u01<Real>(r.b);
     Q.u2 = u01<Real>(r.c);
     Q.u3 = u01<Real>(r.d);
     const int v = q.v;
     const Real E = q.E;
+    Q.beta2 = ph.beta2;
+    Q.ig0 = ph.inv_g0;
+    int bn = -1;
+    if (P.cell_bin) {
+        // per-subcell temperature: the table of the subcell's temperature bin,
+        // tried against the ensemble's Gamma0 (u0 Gamma0_ens / Gamma0_bin)
+        bn = P.cell_bin[(size_t)q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z)];
+        const Phys<Real>& pb = static_cast<const Phys<Real>*>(P.bin_phys)[bn];
+        Q.ig0 = static_cast<const Real*>(P.ens_ig0) + (size_t)q.e * NV;
+        u0 = u0 * static_cast<const Real*>(P.ens_g0)[(size_t)q.e * NV + v] * pb.inv_g0[v];
+        Q.beta2 = pb.beta2;
+    }
     const Real fb = Mth<Real>::floor_(E * K.inv_dE);
     int b;
     if (fb >= Real(K.nb)) {
@@ -376,7 +390,8 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
         b = 0;
         if (!(E == E)) atomicOr(P.err, ERR_NAN);
     }
-    const Real* row = (b < nbs) ? tab_s + ((size_t)v * nbs + b) * NM : tab_g + ((size_t)v * K.nb + b) * NM;
+    const Real* row = (bn >= 0) ? static_cast<const Real*>(P.bin_table) + (((size_t)bn * NV + v) * K.nb + b) * NM
+                    : (b < nbs) ? tab_s + ((size_t)v * nbs + b) * NM : tab_g + ((size_t)v * K.nb + b) * NM;
     int mech = -1;
     if (u0 < row[NM - 1]) {
 #pragma unroll
@@ -400,7 +415,7 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
     }
     if (mech < 0) {
         tally_cnt(bt, P, q.e, e_base, CNT_SELF0 + v, 1u);
-        q.tr = Mth<Real>::neglog_u(Q.u1) * ph.inv_g0[v];
+        q.tr = Mth<Real>::neglog_u(Q.u1) * Q.ig0[v];
     }
     Q.mech = mech;
     return mech;
@@ -433,7 +448,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
     bool rel = true;
     if (mech == 0) {
         // Brooks-Herring: P(cos) ~ 1 / (2k^2 (1 - cos) + beta^2)^2
-        ct = Real(1) - Real(2) * u2 / (Real(1) + Real(4) * k2 * (Real(1) - u2) / ph.beta2);
+        ct = Real(1) - Real(2) * u2 / (Real(1) + Real(4) * k2 * (Real(1) - u2) / Q.beta2);
     } else if (mech <= 2) {
         // Froehlich: P(cos) ~ 1 / (k^2 + k'^2 - 2 k k' cos)
         const Real d = km - kp;
@@ -487,7 +502,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
         agg_add_ll(P.heat, (q.e * K.ncell + c) * 2 + (mech <= 2 ? 0 : 1), d);
     }
     q.v = j;
-    q.tr = Mth<Real>::neglog_u(Q.u1) * ph.inv_g0[j];
+    q.tr = Mth<Real>::neglog_u(Q.u1) * Q.ig0[j];
 }
 
 // Per-thread samples of one ensemble, flushed to the block window (or
@@ -794,7 +809,15 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
             q.seed = P.seed[e];
             q.ctr = P.ctr[slot];
             const Real lo3[3] = {Real(ix * P.dx), Real(iy * P.dy), Real(iz * P.dz)};
-            new_electron<Real, true>(q, ph, lo3, len3, P.err);
+            const Phys<Real>* pi = ph;
+            Phys<Real> pt;
+            if (P.cell_bin) {
+                // thermal at the subcell's temperature; first flight with the ensemble's Gamma0
+                pt = static_cast<const Phys<Real>*>(P.bin_phys)[P.cell_bin[(size_t)e * P.ncell + ix * nface + rem]];
+                for (int vv = 0; vv < NV; ++vv) pt.inv_g0[vv] = static_cast<const Real*>(P.ens_ig0)[(size_t)e * NV + vv];
+                pi = &pt;
+            }
+            new_electron<Real, true>(q, pi, lo3, len3, P.err);
             store<Real>(P, slot, q, true);
             P.tag[slot] = uint32_t(e) << 8;
             atomicAdd(&P.charge[(size_t)e * P.ncell + ix * nface + rem], 1);
@@ -874,6 +897,21 @@ __global__ void k_sort_scatter(const DevParams P, const uint32_t* key, const uns
     const uint32_t id = P.id[p];
     Q.id[d] = id;
     P.slot_of_id[P.ens_off[P.tag[p] >> 8] + id] = uint32_t(d);
+}
+
+// After a change of an ensemble's Gamma0 (new subcell temperatures) the
+// residual flight times are rescaled by Gamma0_old / Gamma0_new of their
+// valley: an exponential residual of rate G_old times G_old / G_new is an
+// exponential of rate G_new, so no redraw is needed.
+template <typename Real>
+__global__ void k_rescale_flights(const DevParams P, int e, const double* ratio)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.ens_cap[e]) return;
+    const int64_t s = P.ens_off[e] + i;
+    const uint32_t tg = P.tag[s];
+    if ((tg & 0xFFu) == DEAD) return;
+    static_cast<Real*>(P.tr)[s] = static_cast<Real*>(P.tr)[s] * Real(ratio[tg & 0xFFu]);
 }
 
 // --------------------------------------------------------------- launch
@@ -957,6 +995,13 @@ void launch_sort(const DevParams& P, const DevParams& alt, bool nw, uint32_t* ke
         if (nw) k_sort_scatter<Real, true><<<grid, 256, 0, st>>>(P, key, offs, cursor, alt);
         else k_sort_scatter<Real, false><<<grid, 256, 0, st>>>(P, key, offs, cursor, alt);
     }
+}
+
+template <typename Real>
+void launch_rescale(const DevParams& P, int e, int64_t cap, const double* ratio, cudaStream_t st)
+{
+    if (cap <= 0) return;
+    k_rescale_flights<Real><<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(P, e, ratio);
 }
 
 template <typename Real>

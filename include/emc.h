@@ -269,6 +269,33 @@ emc_status emc_mlp_params(emc_mlp* m, float* dst, const float* src, int64_t* cou
 const char* emc_mlp_last_error(const emc_mlp* m);
 void emc_mlp_destroy(emc_mlp* m);
 
+/* ------------------------------------------------------------------------
+ * Thermal side of the electrothermal loop: steady Fourier conduction on the
+ * subcell grid with kappa(T) of the paper's phonon model (three identical
+ * sine-shaped acoustic branches omega = omega_max sin(pi q / 2 q0), phonon
+ * relaxation 1/tau = A omega^4 + B1 omega^2 T exp(-B2/T), Table II) plus a
+ * boundary term v_g / L_boundary (the size-modified mean free paths).
+ * Contacts (x = 0, x = L) are held at T_sink; the bottom face (z = 0) loses
+ * heat to T_sink through h_bottom (W/m^2/K); other faces are adiabatic.
+ */
+typedef struct emc_thermal_config {
+    double T_sink;          /* K */
+    double h_bottom;        /* W/(m^2 K) */
+    double L_boundary;      /* m, boundary-scattering length (0: bulk) */
+    double tol_K;           /* Picard stop: max |T_new - T_old| */
+    double k0_per_m, omega_max_rad_s, A_s3, B1_s_per_K, B2_K;  /* Table II column */
+    int32_t max_picard, max_cg;
+} emc_thermal_config;
+
+/* Solve every ensemble of a nanowire context (at most 2048 subcells):
+ * q [E][C] heat generation (W/m^3, host), T [E][C] host: initial guess in,
+ * solution (K) out.  iters (host int[E][2] or NULL): Picard iterations and
+ * total CG iterations per ensemble. */
+emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const double* q, double* T,
+                             int32_t* iters);
+/* kappa(T) (W/m/K) as used by emc_thermal_solve, for n host temperatures. */
+emc_status emc_kappa(const emc_thermal_config* tc, const double* T, double* kappa, int32_t n);
+
 /* Diagnostics used by the test-suite. */
 /* Philox4x32-10 evaluated on the device for n (counter, key) pairs:
  * ctr[n][4], key[n][2] in, out[n][4] out (host arrays). */

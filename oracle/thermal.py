@@ -1,0 +1,91 @@
+"""FP64 reference of the thermal side (test infrastructure only).
+
+kappa(T): kinetic theory over three identical sine-shaped acoustic branches
+omega = omega_max sin(pi q / 2 q0), with 1/tau = A omega^4 + B1 omega^2 T
+exp(-B2/T) (the phonon paragraph and Table II) and, optionally, a boundary
+term v_g / L_b (the size-modified mean free paths of the paragraph after
+Eq. (3)):  kappa = 3 * (1/3) int_0^q0 C(q) v_g(q)^2 tau(q) q^2 / (2 pi^2) dq,
+C(q) = hbar omega dn/dT.
+
+Fourier problem on the subcell grid: sum over faces g_f (T_c - T_n) +
+boundary terms g_b (T_c - T_sink) = q_c, g_f = harmonic-mean kappa / h^2;
+contact faces (x = 0, x = L) at T_sink half a cell away; the bottom face
+(z = 0) through a conductance h_bottom in series with the half cell; other
+faces adiabatic.  kappa(T) by Picard iteration.
+"""
+import numpy as np
+from scipy import constants as sc
+from scipy import integrate, sparse
+from scipy.sparse import linalg as spla
+
+HB, KB = sc.hbar, sc.k
+
+
+def kappa(T, mat, L_b=0.0):
+    q0, wm = mat["k0_per_m"], mat["omega_max_rad_s"]
+    A, B1, B2 = mat["A_s3"], mat["B1_s_per_K"], mat["B2_K"]
+
+    def f(q):
+        w = wm * np.sin(np.pi * q / (2 * q0))
+        vg = wm * np.pi / (2 * q0) * np.cos(np.pi * q / (2 * q0))
+        x = HB * w / (KB * T)
+        dndT = x * np.exp(x) / np.expm1(x) ** 2 / T
+        rate = A * w ** 4 + B1 * w ** 2 * T * np.exp(-B2 / T)
+        if L_b > 0:
+            rate = rate + vg / L_b
+        return HB * w * dndT * vg * vg / rate * q * q / (2 * np.pi ** 2)
+
+    return integrate.quad(f, 0.0, q0, epsabs=0, epsrel=1e-10, limit=400)[0]
+
+
+def operator(cfg, kap, T_sink, h_bottom):
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    hx, hy, hz = cfg["Lx"] / nx, cfg["Ly"] / ny, cfg["Lz"] / nz
+    n = nx * ny * nz
+    idx = lambda i, j, l: (i * ny + j) * nz + l
+    rows, cols, vals = [], [], []
+    diag = np.zeros(n)
+    rhs_b = np.zeros(n)
+    for i in range(nx):
+        for j in range(ny):
+            for l in range(nz):
+                c = idx(i, j, l)
+                kc = kap[c]
+                for (di, dj, dl, h) in ((1, 0, 0, hx), (-1, 0, 0, hx), (0, 1, 0, hy), (0, -1, 0, hy),
+                                        (0, 0, 1, hz), (0, 0, -1, hz)):
+                    ii, jj, ll = i + di, j + dj, l + dl
+                    if 0 <= ii < nx and 0 <= jj < ny and 0 <= ll < nz:
+                        nb = idx(ii, jj, ll)
+                        g = 2 * kc * kap[nb] / (kc + kap[nb]) / h ** 2
+                        diag[c] += g
+                        rows.append(c); cols.append(nb); vals.append(-g)
+                    elif di != 0:  # contact faces: Dirichlet at T_sink
+                        g = 2 * kc / h ** 2
+                        diag[c] += g
+                        rhs_b[c] += g * T_sink
+                    elif dl == -1:  # bottom face: conductance to the sink
+                        g = 1.0 / (h * (h / (2 * kc) + 1.0 / h_bottom))
+                        diag[c] += g
+                        rhs_b[c] += g * T_sink
+    A = sparse.csr_matrix((vals + list(diag), (rows + list(range(n)), cols + list(range(n)))), shape=(n, n))
+    return A, rhs_b
+
+
+def solve(cfg, q, mat, T_sink=300.0, h_bottom=1e9, L_b=0.0, tol=1e-8, max_picard=50, T0=None):
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    T = np.full(n, T_sink) if T0 is None else np.array(T0, dtype=float)
+    cache = {}
+    def kap_of(t):
+        key = round(float(t), 9)
+        if key not in cache:
+            cache[key] = kappa(t, mat, L_b)
+        return cache[key]
+    for _ in range(max_picard):
+        kap = np.array([kap_of(t) for t in T])
+        A, b = operator(cfg, kap, T_sink, h_bottom)
+        Tn = spla.spsolve(A.tocsc(), q + b)
+        done = np.abs(Tn - T).max() < tol
+        T = Tn
+        if done:
+            break
+    return T

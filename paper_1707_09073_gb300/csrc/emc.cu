@@ -1362,6 +1362,21 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
 
 }  // extern "C"
 
+// accessors used by the thermal unit
+namespace emc {
+cudaStream_t ctx_stream(emc_ctx* ctx) { return ctx->st; }
+int ctx_grid(emc_ctx* ctx, int* nx, int* ny, int* nz, double* Lx, double* Ly, double* Lz, int* n_ens)
+{
+    if (ctx->geom != EMC_GEOM_NANOWIRE) return 0;
+    *nx = ctx->nx; *ny = ctx->ny; *nz = ctx->nz;
+    *Lx = ctx->cfg[0].Lx; *Ly = ctx->cfg[0].Ly; *Lz = ctx->cfg[0].Lz;
+    *n_ens = ctx->n_ens;
+    return 1;
+}
+emc_status ctx_fail(emc_ctx* ctx, emc_status s, const char* msg) { return fail(ctx, s, msg); }
+void ctx_count_launches(emc_ctx* ctx, int64_t n) { ctx->launches += n; }
+}  // namespace emc
+
 // ------------------------------------------- allocation-free Poisson solve
 // Scratch of emc_poisson_solve_static: right-hand side, potential and charge
 // density (double[kStaticCells] each), the three terminal voltages, and the

@@ -280,6 +280,54 @@ def obs_dict(o: EmcObs) -> dict:
     }
 
 
+# ------------------------------------------------------------ thermal side
+class EmcThermalConfig(C.Structure):
+    _fields_ = [("T_sink", C.c_double), ("h_bottom", C.c_double), ("L_boundary", C.c_double), ("tol_K", C.c_double),
+                ("k0_per_m", C.c_double), ("omega_max_rad_s", C.c_double), ("A_s3", C.c_double),
+                ("B1_s_per_K", C.c_double), ("B2_K", C.c_double), ("max_picard", C.c_int32), ("max_cg", C.c_int32)]
+
+
+def thermal_config(table_ii: dict, T_sink=300.0, h_bottom=1e9, L_boundary=120e-9, tol_K=1e-6, max_picard=50,
+                   max_cg=5000) -> EmcThermalConfig:
+    t = EmcThermalConfig()
+    t.T_sink, t.h_bottom, t.L_boundary, t.tol_K = T_sink, h_bottom, L_boundary, tol_K
+    t.k0_per_m, t.omega_max_rad_s = table_ii["k0_per_m"], table_ii["omega_max_rad_s"]
+    t.A_s3, t.B1_s_per_K, t.B2_K = table_ii["A_s3"], table_ii["B1_s_per_K"], table_ii["B2_K"]
+    t.max_picard, t.max_cg = max_picard, max_cg
+    return t
+
+
+def _thermal_lib():
+    L = lib()
+    if not getattr(L, "_thermal_ready", False):
+        dp = C.POINTER(C.c_double)
+        L.emc_thermal_solve.argtypes = [C.c_void_p, C.POINTER(EmcThermalConfig), dp, dp, C.POINTER(C.c_int32)]
+        L.emc_thermal_solve.restype = C.c_int
+        L.emc_kappa.argtypes = [C.POINTER(EmcThermalConfig), dp, dp, C.c_int32]
+        L.emc_kappa.restype = C.c_int
+        L._thermal_ready = True
+    return L
+
+
+def kappa(tc: EmcThermalConfig, T) -> np.ndarray:
+    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    out = np.zeros_like(T)
+    st = _thermal_lib().emc_kappa(C.byref(tc), _p(T), _p(out), T.size)
+    if st != 0:
+        raise EmcError(st, "emc_kappa")
+    return out
+
+
+def thermal_solve(ctx: "Context", tc: EmcThermalConfig, q, T0=None):
+    """Temperature [E][C] of every ensemble of a nanowire context for heat
+    generation q [E][C] (W/m^3)."""
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(ctx.n_ens, ctx.n_cell)
+    T = np.full_like(q, tc.T_sink) if T0 is None else np.ascontiguousarray(T0, dtype=np.float64).copy()
+    it = np.zeros((ctx.n_ens, 2), dtype=np.int32)
+    ctx._check(_thermal_lib().emc_thermal_solve(ctx.h, C.byref(tc), _p(q), _p(T), _p(it, C.c_int32)))
+    return T, it
+
+
 # ------------------------------------------------------------ surrogate MLP
 class EmcMlpConfig(C.Structure):
     _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_layers", C.c_int32), ("n_out", C.c_int32),

@@ -1,0 +1,51 @@
+"""Thermal side on the GPU against the reference, and the coupled
+electrothermal iteration with and without the surrogate warm start."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import thermal as tref
+
+pytestmark = pytest.mark.gpu
+
+
+def test_thermal_solve_matches_reference(emc):
+    cfgs = [W.nanowire(n_particles=100, nx=20, Lx=200e-9, Vd=1.0, seed=s) for s in range(2)]
+    tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=2e8, L_boundary=120e-9, tol_K=1e-9)
+    rng = np.random.default_rng(0)
+    with emc.Context(cfgs) as ctx:
+        q = rng.uniform(0, 2e18, size=(2, ctx.n_cell))
+        T, it = emc.emc.thermal_solve(ctx, tc, q)
+    for e in range(2):
+        want = tref.solve(cfgs[e], q[e], W.TABLE_II_GAN, h_bottom=2e8, L_b=120e-9, tol=1e-9)
+        np.testing.assert_allclose(T[e] - 300.0, want - 300.0, rtol=1e-5)
+    assert (it[:, 0] > 1).all()
+
+
+def test_electrothermal_warm_start(emc):
+    """The plain Monte Carlo iteration and the surrogate-started one reach
+    the same peak temperature rise (within 2% or the Monte Carlo noise); the
+    warm start needs no more Monte Carlo iterations."""
+    from paper_1707_09073_gb300 import electrothermal as ET
+    from paper_1707_09073_gb300 import surrogate as S
+    base = W.bulk()
+    X = S.sample_inputs(3072, seed=11)
+    Y = S.mc_observables(X, base, n_electrons=2000, warm_steps=800, avg_steps=800, seed0=7)
+    sur = S.Surrogate(X, Y, seed=5)
+    sur.fit(X, Y, steps=3000, batch=1024, lr=2e-3, seed=6)
+    cfgs = [W.nanowire(n_particles=40_000, nx=20, Lx=200e-9, Vd=float(v), seed=50 + v) for v in (2, 4)]
+    tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=1e9, L_boundary=120e-9, tol_K=1e-3)
+    with emc.Context(cfgs) as ctx:
+        ctx.emc_step(500)
+        plain = ET.iterate(ctx, tc, np.full((2, ctx.n_cell), 300.0), max_iter=12, rtol=0.01)
+    with emc.Context(cfgs) as ctx:
+        ctx.emc_step(500)
+        T0, t_sur = ET.surrogate_start(ctx, sur, tc)
+        warm = ET.iterate(ctx, tc, T0, max_iter=12, rtol=0.01)
+    assert plain["converged"] and warm["converged"], (plain["history"], warm["history"])
+    assert warm["iterations"] <= plain["iterations"], (plain["history"], warm["history"])
+    assert np.all(np.abs(warm["peak"] - plain["peak"]) <= np.maximum(0.03 * plain["peak"], 0.5)), \
+        (warm["peak"], plain["peak"])
+    assert (plain["peak"] > 1.0).all()

@@ -203,6 +203,70 @@ def run_reference(args, world: int, rank: int):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- surrogate vs plain MC
+def electrothermal_comparison(args, stream) -> dict:
+    """Convergence of the coupled electrothermal iteration on the half
+    nanowire at 64 drain biases (0..20 V) with 1800 subcells: plain Monte
+    Carlo from a uniform 300 K start vs the surrogate warm start (surrogate
+    trained on this library's own bulk Monte Carlo data, its data and
+    training time counted separately).  Peak temperature rises are compared
+    at convergence (the Monte Carlo stays the judge)."""
+    import numpy as np
+    import paper_1707_09073_gb300 as emc
+    from paper_1707_09073_gb300 import electrothermal as ET
+    from paper_1707_09073_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    X = S.sample_inputs(args.sur_samples, seed=11)
+    Y = S.mc_observables(X, W.bulk(), n_electrons=2000, warm_steps=800, avg_steps=800, seed0=7,
+                         stream=stream.cuda_stream)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sur = S.Surrogate(X, Y, seed=5, stream=stream.cuda_stream)
+    sur.fit(X, Y, steps=3000, batch=1024, lr=2e-3, seed=6)
+    t_train = time.perf_counter() - t0
+    nb = args.et_biases
+    cfgs = [W.nanowire(n_particles=args.et_particles, Vd=20.0 * i / (nb - 1), seed=500 + i) for i in range(nb)]
+    tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=args.h_bottom, L_boundary=120e-9, tol_K=1e-3)
+    out = {}
+    for mode in ("plain", "surrogate"):
+        ctx = emc.Context(cfgs, stream=stream.cuda_stream)
+        try:
+            ctx.emc_step(500)
+            t0 = time.perf_counter()
+            if mode == "plain":
+                r = ET.iterate(ctx, tc, np.full((nb, ctx.n_cell), 300.0), max_iter=15, rtol=0.01)
+                t_sur = 0.0
+            else:
+                r = ET.surrogate_accelerated(ctx, sur, tc, max_iter=15, rtol=0.01)
+                t_sur = r["surrogate_seconds"]
+            out[mode] = {"converged": r["converged"], "mc_iterations": r["iterations"],
+                         "seconds": time.perf_counter() - t0, "surrogate_seconds": t_sur,
+                         "peak_rise_K_max_bias": float(r["peak"][-1]),
+                         "peak_rise_K_max_bias_history": [round(float(h[-1]), 2) for h in r["history"]],
+                         "peak": r["peak"]}
+            if mode != "plain":
+                out[mode]["predicted_peak_rise_K_max_bias"] = float(r["predicted_peak"][-1])
+        finally:
+            ctx.close()
+    dp = out["surrogate"]["peak"] - out["plain"]["peak"]
+    hot = out["plain"]["peak"] > 1.0
+    res = {
+        "workload": "half nanowire 3x6x100, %d drain biases 0..20 V x %d superparticles, Fourier with kappa(T) "
+                    "(Table II, 120 nm boundary), h_bottom %.1e W/m2/K; converged when every peak rise changes "
+                    "< max(1%%, 0.5 K) between iterations; surrogate run: Monte Carlo iteration 1 at 300 K, then the "
+                    "surrogate's current-vs-temperature response jumps to a predicted self-consistent field, then "
+                    "Monte Carlo iterations until stationary" % (nb, args.et_particles, args.h_bottom),
+        "plain_mc": {k: v for k, v in out["plain"].items() if k != "peak"},
+        "surrogate_warm_start": {k: v for k, v in out["surrogate"].items() if k != "peak"},
+        "speedup": out["plain"]["seconds"] / max(out["surrogate"]["seconds"], 1e-9),
+        "peak_rise_max_rel_diff": float(np.max(np.abs(dp[hot]) / out["plain"]["peak"][hot])) if hot.any() else None,
+        "peak_rise_rel_diff_max_bias": float(abs(dp[-1]) / max(out["plain"]["peak"][-1], 1e-9)),
+        "surrogate": {"samples": args.sur_samples, "data_seconds": t_data, "train_seconds": t_train,
+                      "network": "4-128-128-128-7 SiLU, BF16 tensor cores, FP32 accumulation"},
+    }
+    return res
+
+
 # --------------------------------------------------------------------- GPU
 def run_emc(args, world: int, rank: int, local: int):
     import numpy as np
@@ -321,6 +385,11 @@ def run_emc(args, world: int, rank: int, local: int):
                "sample": "FP64 oracle, single thread: 1 of the 21 bias points (V_d = 10 V), %d superparticles, "
                          "%d Poisson periods (%.1f s)" % (s["n_particles"], s["periods"], s["seconds"])}
 
+    et = None
+    if world == 1 and not args.no_electrothermal:
+        torch.cuda.synchronize(dev)
+        et = electrothermal_comparison(args, stream)
+
     cfg = workload_desc(n_part)
     cfg["parallelism"] = "weak: one full sweep per GPU" if world > 1 else "1 GPU"
     cfg["launch"] = dict(tune, source="autotuner" if tuned else ("command line" if tune else "defaults"))
@@ -337,6 +406,7 @@ def run_emc(args, world: int, rank: int, local: int):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
                    "samples": clocks["samples"]},
         "gpu_launches": launches,
+        "surrogate_vs_plain_mc": et,
     }
     print(json.dumps(line), flush=True)
 
@@ -356,6 +426,11 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="flight-kernel block size (0 = default)")
     ap.add_argument("--sort-period", type=int, default=0, help="sort particles every this many launches (0 = never)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--no-electrothermal", action="store_true", help="skip the surrogate vs plain-MC comparison")
+    ap.add_argument("--et-biases", type=int, default=64)
+    ap.add_argument("--et-particles", type=int, default=100_000)
+    ap.add_argument("--sur-samples", type=int, default=8192)
+    ap.add_argument("--h-bottom", type=float, default=5e8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

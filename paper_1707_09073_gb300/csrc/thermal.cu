@@ -14,7 +14,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/emc.h"
@@ -38,7 +41,7 @@ constexpr int kMaxThermalCells = 2048;
 
 // kappa(T) of the GaN column of Table II on the grid above (midpoint rule in
 // the wave vector, 4000 points)
-std::vector<double> kappa_table(const emc_thermal_config& tc)
+std::vector<double> kappa_table_build(const emc_thermal_config& tc)
 {
     const double q0 = tc.k0_per_m, wm = tc.omega_max_rad_s;
     std::vector<double> out(kNT);
@@ -60,6 +63,18 @@ std::vector<double> kappa_table(const emc_thermal_config& tc)
         out[t] = acc * q0 / nq;
     }
     return out;
+}
+
+// tables are cached per phonon parameter set (the quadrature costs ~0.3 s)
+std::vector<double> kappa_table(const emc_thermal_config& tc)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<double, double, double, double, double, double>, std::vector<double>> cache;
+    const auto key = std::make_tuple(tc.k0_per_m, tc.omega_max_rad_s, tc.A_s3, tc.B1_s_per_K, tc.B2_K, tc.L_boundary);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) it = cache.emplace(key, kappa_table_build(tc)).first;
+    return it->second;
 }
 
 struct TGeo {

@@ -1,15 +1,16 @@
 """The coupled electrothermal iteration of the hybrid method and its
-surrogate warm start.
+surrogate-accelerated variant.
 
 Plain iteration (the paragraph ending "until the steady-state temperature
 distribution is obtained"): electron Monte Carlo at the current subcell
 temperatures -> heat generated per subcell (net phonon emission) -> Fourier
 solve -> new subcell temperatures, repeated until the peak temperature rise
-stops changing.  Warm start: before the first Monte Carlo run, the surrogate
-predicts the heat of every subcell from its local field, temperature and
-doping (local-field approximation), iterated with the Fourier solve to a
-self-consistent first guess of the temperatures; the Monte Carlo iteration
-then starts there and remains the judge of the result.
+stops changing.  Accelerated iteration: after the first Monte Carlo run the
+surrogate's drift velocity v_d(E, T) predicts how the device current, and so
+the heat, responds to the temperature field; that prediction is iterated with
+the Fourier solve to a first guess of the self-consistent temperatures, and
+the Monte Carlo iteration continues from there and remains the judge of the
+result.
 """
 from __future__ import annotations
 
@@ -44,21 +45,23 @@ def peak_rise(T: np.ndarray, T_sink: float) -> np.ndarray:
     return T.max(axis=1) - T_sink
 
 
-def iterate(ctx, tc, T0: np.ndarray, warm_steps: int = 300, avg_steps: int = 600, max_iter: int = 12,
-            rtol: float = 0.01, relax: float = 1.0) -> dict:
-    """Monte Carlo <-> Fourier fixed point from T0; converged when every
-    ensemble's peak rise changes by less than rtol between iterations."""
+def iterate(ctx, tc, T0: np.ndarray, warm_steps: int = 300, avg_steps: int = 1000, max_iter: int = 12,
+            rtol: float = 0.01, atol: float = 0.5, relax: float = 1.0, prev_peak=None) -> dict:
+    """Monte Carlo <-> Fourier fixed point from T0; converged when the peak
+    temperature rise of the device (the largest over all bias points and
+    subcells) changes by less than max(rtol * rise, atol kelvin) between
+    iterations."""
     T = np.array(T0, dtype=float)
     hist = []
     t0 = time.perf_counter()
-    prev = None
+    prev = prev_peak
     for it in range(1, max_iter + 1):
         q = mc_heat(ctx, T, warm_steps, avg_steps)
         Tn, _ = _emc.thermal_solve(ctx, tc, q, T)
         T = T + relax * (Tn - T)
         pk = peak_rise(T, tc.T_sink)
         hist.append(pk.copy())
-        if prev is not None and np.all(np.abs(pk - prev) <= rtol * np.maximum(np.abs(pk), 1e-9)):
+        if prev is not None and abs(pk.max() - prev.max()) <= max(rtol * abs(pk.max()), atol):
             return {"converged": True, "iterations": it, "T": T, "peak": pk, "history": hist,
                     "seconds": time.perf_counter() - t0}
         prev = pk
@@ -66,28 +69,80 @@ def iterate(ctx, tc, T0: np.ndarray, warm_steps: int = 300, avg_steps: int = 600
             "seconds": time.perf_counter() - t0}
 
 
-def surrogate_start(ctx, sur, tc, sweeps: int = 8) -> tuple[np.ndarray, float]:
-    """First guess of the subcell temperatures from the surrogate: local
-    |E|, field angle to the c axis, T and N_d of every subcell -> heat per
-    electron, times the subcell electron density; alternated with the Fourier
-    solve.  Returns the temperatures and the seconds spent."""
+def _invert(v: np.ndarray, Eg: np.ndarray, target: np.ndarray) -> np.ndarray:
+    """Field at which the increasing velocity curves v[..., :] (sampled at
+    Eg) reach target[...] (linear interpolation, clamped to the grid)."""
+    n = v.shape[-1]
+    k = np.clip((v < target[..., None]).sum(axis=-1), 1, n - 1)
+    v0 = np.take_along_axis(v, (k - 1)[..., None], -1)[..., 0]
+    v1 = np.take_along_axis(v, k[..., None], -1)[..., 0]
+    a = np.clip((target - v0) / np.maximum(v1 - v0, 1e-30), 0.0, 1.0)
+    return Eg[k - 1] + a * (Eg[k] - Eg[k - 1])
+
+
+def current_ratio(ctx, sur, T: np.ndarray, E0: np.ndarray, T0: float, n_grid: int = 128) -> np.ndarray:
+    """Ratio r = J(T) / J(T0) of the device current under the temperature
+    field T, from the surrogate's drift velocity: every x-slice keeps the
+    Monte Carlo field E0_i it had at the uniform temperature T0 as its
+    operating point, its field at T solves v_d(E_i, T_i) = r v_d(E0_i, T0)
+    (increasing branch of v_d(E)), and r is the value for which the voltage
+    sum_i E_i dx is unchanged (current continuity along the wire)."""
+    from .surrogate import BOX, OUT_NAMES
+    c0 = ctx.cfgs[0]
+    nx, nyz = c0["nx"], c0["ny"] * c0["nz"]
+    E0 = np.minimum(E0, BOX["E_max"])
+    Eg = np.concatenate([[0.0], np.geomspace(1e3, BOX["E_max"], n_grid - 1)])
+    jv = OUT_NAMES.index("v_drift_m_s")
+    Ts = T.reshape(ctx.n_ens, nx, nyz).mean(axis=2)
+    X = np.empty((ctx.n_ens, nx, n_grid + 1, 4), dtype=np.float32)
+    X[..., :n_grid, 0] = Eg[None, None, :]
+    X[..., n_grid, 0] = E0
+    X[..., 1] = 0.0
+    X[..., :n_grid, 2] = Ts[:, :, None]
+    X[..., n_grid, 2] = T0
+    for e, c in enumerate(ctx.cfgs):
+        X[e, ..., 3] = math.log10(c["Nd"])
+    out = sur.predict(X.reshape(-1, 4))[:, jv].reshape(ctx.n_ens, nx, n_grid + 1)
+    v = np.maximum.accumulate(np.maximum(out[..., :n_grid], 0.0), axis=2)
+    v0 = np.minimum(np.maximum(out[..., n_grid], 0.0), v[..., -1])
+    V0 = E0.sum(axis=1)
+    lo, hi = np.zeros(ctx.n_ens), np.full(ctx.n_ens, 4.0)
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        Vm = _invert(v, Eg, mid[:, None] * v0).sum(axis=1)
+        low = Vm < V0
+        lo = np.where(low, mid, lo)
+        hi = np.where(low, hi, mid)
+    r = 0.5 * (lo + hi)
+    return np.where((V0 > 0) & (v0.max(axis=1) > 0), r, 1.0)
+
+
+def surrogate_accelerated(ctx, sur, tc, T_start: float = None, warm_steps: int = 300, avg_steps: int = 1000,
+                          max_iter: int = 12, rtol: float = 0.01, atol: float = 0.5, sweeps: int = 10) -> dict:
+    """Electrothermal iteration accelerated by the surrogate.  Monte Carlo
+    iteration 1 at the uniform start temperature gives the heat map q1 (the
+    plain iteration's first step too).  The surrogate then predicts how the
+    device current responds to the temperature field, J(T) / J(T_start)
+    (current_ratio), and q = q1 J(T) / J(T_start) is iterated with the Fourier
+    solve to a predicted self-consistent temperature field -- the step the
+    plain fixed-point iteration takes many Monte Carlo runs to make.  Monte
+    Carlo iterations continue from there until the peak rise is stationary;
+    the Monte Carlo remains the judge of the result."""
+    T_start = tc.T_sink if T_start is None else T_start
     t0 = time.perf_counter()
-    E = ctx.emc_tally(_emc.TALLY_FIELD)                  # [E][C][3] V/m
-    n_cnt = ctx.emc_tally(_emc.TALLY_CHARGE).astype(float)
-    Em = np.linalg.norm(E, axis=2)
-    ang = np.arccos(np.clip(np.abs(E[..., 2]) / np.maximum(Em, 1e-30), 0.0, 1.0))
-    T = np.full((ctx.n_ens, ctx.n_cell), tc.T_sink)
-    j_heat = 5
+    T = np.full((ctx.n_ens, ctx.n_cell), T_start)
+    q1 = mc_heat(ctx, T, warm_steps, avg_steps)
+    ts = time.perf_counter()
+    c0 = ctx.cfgs[0]
+    E0 = np.abs(ctx.emc_tally(_emc.TALLY_FIELD)[..., 0]).reshape(ctx.n_ens, c0["nx"], -1).mean(axis=2)
+    Tp, _ = _emc.thermal_solve(ctx, tc, q1, T)
     for _ in range(sweeps):
-        rows = []
-        for e, c in enumerate(ctx.cfgs):
-            rows.append(np.stack([Em[e], ang[e], T[e], np.full(ctx.n_cell, math.log10(c["Nd"]))], axis=1))
-        X = np.concatenate(rows).astype(np.float32)
-        h = sur.predict(X)[:, j_heat].reshape(ctx.n_ens, ctx.n_cell)
-        q = np.empty_like(h)
-        for e, c in enumerate(ctx.cfgs):
-            Vc = c["Lx"] * c["Ly"] * c["Lz"] / ctx.n_cell
-            w = c["Nd"] * c["Lx"] * c["Ly"] * c["Lz"] / c["n_particles"]
-            q[e] = np.maximum(h[e], 0.0) * w * n_cnt[e] / Vc
-        T, _ = _emc.thermal_solve(ctx, tc, q, T)
-    return T, time.perf_counter() - t0
+        ratio = current_ratio(ctx, sur, Tp, E0, T_start)
+        Tp, _ = _emc.thermal_solve(ctx, tc, q1 * ratio[:, None], Tp)
+    t_sur = time.perf_counter() - ts
+    r = iterate(ctx, tc, Tp, warm_steps, avg_steps, max_iter - 1, rtol, atol, prev_peak=peak_rise(Tp, tc.T_sink))
+    r["iterations"] += 1
+    r["seconds"] = time.perf_counter() - t0
+    r["surrogate_seconds"] = t_sur
+    r["predicted_peak"] = peak_rise(Tp, tc.T_sink)
+    return r

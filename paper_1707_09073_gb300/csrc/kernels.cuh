@@ -138,6 +138,7 @@ __device__ __forceinline__ void agg_add_i(int* base, int key)
 template <typename Real>
 struct Part {
     Real kx, ky, kz, x, y, z, tr, E;  // E: kinetic energy of k, carried along
+    Real f;                           // hbar/(m(1 + 2 alpha E)): v = f k, carried with E
     uint64_t ctr;
     uint32_t id, seed;
     int v, e;
@@ -253,10 +254,9 @@ __device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>& ph, const
     const Real E0 = q.E;
     const Real E1 = kane_E(ph.ck[v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), al);
     q.E = E1;
+    const Real f1 = ph.vk[v] / (Real(1) + Real(2) * al * E1);
     if (NW) {
-        const Real vk = ph.vk[v];
-        const Real f0 = vk / (Real(1) + Real(2) * al * E0);
-        const Real f1 = vk / (Real(1) + Real(2) * al * E1);
+        const Real f0 = q.f;
         const Real h = Real(0.5) * t;
         Real dx = h * (f0 * k0x + f1 * q.kx);
         Real dy = h * (f0 * k0y + f1 * q.ky);
@@ -274,6 +274,7 @@ __device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>& ph, const
         q.y += dy;
         q.z += dz;
     }
+    q.f = f1;
 }
 
 // ------------------------------------------------------------- walls
@@ -490,6 +491,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
     q.ky = kp * dy;
     q.kz = kp * dz;
     q.E = Ep;
+    q.f = ph.vk[j] / (Real(1) + Real(2) * ph.alpha[j] * Ep);
     const int w = q.e - e_base;
     if (w >= 0 && w < WE)
         atomicAdd(&bt->ev[w][v * NM + mech], 1u);
@@ -534,6 +536,43 @@ struct Samples {
         Et.clear();
         nv[0] = nv[1] = nv[2] = 0u;
     }
+};
+
+// Samples of one particle over the steps of a launch.  Float build: plain
+// float partial sums over the (at most a few tens of) steps, folded into the
+// thread's compensated accumulators once per particle; double build: added
+// to the accumulators directly, in step order.
+template <typename Real>
+struct StepSums {
+    Real v0 = 0, v1 = 0, v2 = 0, E = 0, Et = 0;
+    __device__ __forceinline__ void add(Samples<Real>&, Real a, Real b, Real c, Real d, Real e)
+    {
+        v0 += a;
+        v1 += b;
+        v2 += c;
+        E += d;
+        Et += e;
+    }
+    __device__ __forceinline__ void fold(Samples<Real>& S) const
+    {
+        S.v[0].add(v0);
+        S.v[1].add(v1);
+        S.v[2].add(v2);
+        S.E.add(E);
+        S.Et.add(Et);
+    }
+};
+template <>
+struct StepSums<double> {
+    __device__ __forceinline__ void add(Samples<double>& S, double a, double b, double c, double d, double e)
+    {
+        S.v[0].add(a);
+        S.v[1].add(b);
+        S.v[2].add(c);
+        S.E.add(d);
+        S.Et.add(e);
+    }
+    __device__ __forceinline__ void fold(Samples<double>&) const {}
 };
 
 // -------------------------------------------------------------- flight
@@ -634,13 +673,22 @@ __global__ void __launch_bounds__(256, 3)
         const Phys<Real>& ph = (ts < K.n_tab_s) ? ph_s[ts] : ph_g[ts];
         const Real* tab_g = tab_all + (size_t)ts * NV * K.nb * NM;
         q.E = kane_E(ph.ck[q.v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), ph.alpha[q.v]);
+        q.f = ph.vk[q.v] / (Real(1) + Real(2) * ph.alpha[q.v] * q.E);
         Real f4[4];
         if (!NW) load4<Real>(static_cast<const Real*>(P.acc_bulk) + 4 * (size_t)q.e, f4);
+        int cell = -1;
+        StepSums<Real> ss;
         bool live = true;
         for (int s = 0; s < n_steps && live; ++s) {
-            if (NW)
-                load4<Real>(static_cast<const Real*>(P.acc_cell) +
-                                4 * ((size_t)q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z)), f4);
+            if (NW) {
+                // the field of the subcell at the start of the step (reloaded
+                // only when the particle has changed subcell)
+                const int c = cell_of<Real>(K, q.x, q.y, q.z);
+                if (c != cell) {
+                    load4<Real>(static_cast<const Real*>(P.acc_cell) + 4 * ((size_t)q.e * K.ncell + c), f4);
+                    cell = c;
+                }
+            }
             Real tleft = dt;
             for (int it = 0;; ++it) {
                 if (it >= MAX_FLIGHTS_PER_STEP) {
@@ -663,14 +711,10 @@ __global__ void __launch_bounds__(256, 3)
             }
             if (!live) break;
             const int v = q.v;
-            const Real f = ph.vk[v] / (Real(1) + Real(2) * ph.alpha[v] * q.E);
-            S.v[0].add(f * q.kx);
-            S.v[1].add(f * q.ky);
-            S.v[2].add(f * q.kz);
-            S.E.add(q.E);
-            S.Et.add(q.E + ph.Ec[v]);
+            ss.add(S, q.f * q.kx, q.f * q.ky, q.f * q.kz, q.E, q.E + ph.Ec[v]);
             S.nv[v] += 1u;
         }
+        ss.fold(S);
         store<Real>(P, p, q, NW);
         P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
         if (NW && count_charge && live) agg_add_i(P.charge, q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z));

@@ -72,6 +72,7 @@ struct Acc {
         s = t;
     }
     __device__ __forceinline__ double value() const { return double(s) - double(c); }
+    __device__ __forceinline__ Real comp() const { return c; }
     __device__ __forceinline__ void clear() { s = c = 0; }
 };
 template <>
@@ -79,6 +80,7 @@ struct Acc<double> {
     double s = 0;
     __device__ __forceinline__ void add(double x) { s += x; }
     __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ double comp() const { return 0.0; }
     __device__ __forceinline__ void clear() { s = 0; }
 };
 
@@ -507,34 +509,69 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
     q.tr = Mth<Real>::neglog_u(Q.u1) * Q.ig0[j];
 }
 
-// Per-thread samples of one ensemble, flushed to the block window (or
-// global memory) when the thread moves on to another ensemble.
+// Per-thread samples of one ensemble.  When threads move on to another
+// ensemble, the warp flushes them together: the threads holding the same
+// ensemble are summed across the warp (float tree of the compensated sums,
+// integer warp reduction of the counts) and one of them adds the result to
+// the block window (or global memory), so no two lanes of a warp contend for
+// one tally word.
+template <typename Real>
+__device__ __forceinline__ Real warp_sum(Real x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 template <typename Real>
 struct Samples {
     Acc<Real> v[3], E, Et;
     unsigned int nv[NV] = {0u, 0u, 0u};
     int e = -1;
 
-    __device__ __forceinline__ void flush(const DevParams& P, BlockTally* bt, int e_base)
+    // Called by all 32 lanes of the warp; lanes with `need` set hand over
+    // their samples and start afresh.
+    __device__ __forceinline__ void flush_warp(const DevParams& P, BlockTally* bt, int e_base, bool need)
     {
-        const unsigned int n = nv[0] + nv[1] + nv[2];
-        if (e >= 0 && n > 0u) {
-            const double vals[5] = {v[0].value(), v[1].value(), v[2].value(), E.value(), Et.value()};
-            const int w = e - e_base;
-            if (w >= 0 && w < WE) {
-                for (int i = 0; i < 5; ++i) atomicAdd(&bt->sums[w][i], vals[i]);
-                for (int i = 0; i < NV; ++i) atomicAdd(&bt->cnt[w][CNT_V0 + i], nv[i]);
-                atomicAdd(&bt->cnt[w][CNT_SAMPLES], n);
-            } else {
-                for (int i = 0; i < 5; ++i) atomicAdd(&P.sums[(size_t)e * NSUM + i], vals[i]);
-                for (int i = 0; i < NV; ++i) atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_V0 + i], (unsigned long long)nv[i]);
-                atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_SAMPLES], (unsigned long long)n);
+        const bool mine = need && e >= 0 && (nv[0] + nv[1] + nv[2]) > 0u;
+        unsigned pending = __ballot_sync(0xffffffffu, mine);
+        while (pending) {
+            const int key = __shfl_sync(0xffffffffu, e, __ffs(pending) - 1);
+            const bool in = mine && e == key;
+            const unsigned grp = __ballot_sync(0xffffffffu, in);
+            const Acc<Real>* a[5] = {&v[0], &v[1], &v[2], &E, &Et};
+            double vals[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const Real ss = warp_sum<Real>(in ? a[i]->s : Real(0));
+                const Real cc = warp_sum<Real>(in ? Real(a[i]->comp()) : Real(0));
+                vals[i] = double(ss) - double(cc);
             }
+            unsigned int cnt[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) cnt[i] = __reduce_add_sync(0xffffffffu, in ? nv[i] : 0u);
+            if ((threadIdx.x & 31) == __ffs(grp) - 1) {
+                const unsigned int n = cnt[0] + cnt[1] + cnt[2];
+                const int w = key - e_base;
+                if (w >= 0 && w < WE) {
+                    for (int i = 0; i < 5; ++i) atomicAdd(&bt->sums[w][i], vals[i]);
+                    for (int i = 0; i < NV; ++i) atomicAdd(&bt->cnt[w][CNT_V0 + i], cnt[i]);
+                    atomicAdd(&bt->cnt[w][CNT_SAMPLES], n);
+                } else {
+                    for (int i = 0; i < 5; ++i) atomicAdd(&P.sums[(size_t)key * NSUM + i], vals[i]);
+                    for (int i = 0; i < NV; ++i)
+                        atomicAdd(&P.cnt[(size_t)key * NCNT + CNT_V0 + i], (unsigned long long)cnt[i]);
+                    atomicAdd(&P.cnt[(size_t)key * NCNT + CNT_SAMPLES], (unsigned long long)n);
+                }
+            }
+            pending &= ~grp;
         }
-        for (int i = 0; i < 3; ++i) v[i].clear();
-        E.clear();
-        Et.clear();
-        nv[0] = nv[1] = nv[2] = 0u;
+        if (need) {
+            for (int i = 0; i < 3; ++i) v[i].clear();
+            E.clear();
+            Et.clear();
+            nv[0] = nv[1] = nv[2] = 0u;
+        }
     }
 };
 
@@ -644,17 +681,18 @@ __global__ void __launch_bounds__(256, 3)
     Samples<Real> S;
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
         const int64_t p = c * 32 + lane;
-        if (p >= P.n_slots) continue;
-        const uint32_t tg = P.tag[p];
-        if ((tg & 0xFFu) == DEAD) continue;
+        const uint32_t tg = (p < P.n_slots) ? P.tag[p] : uint32_t(DEAD);
+        const bool valid = (tg & 0xFFu) != DEAD;
+        // lanes whose samples belong to another ensemble than their new
+        // particle hand them over (warp-wide, all lanes converged here)
+        const bool need = valid && int(tg >> 8) != S.e;
+        if (__any_sync(0xffffffffu, need)) S.flush_warp(P, bt, e_base, need);
+        if (!valid) continue;
         QEntry<Real> Q;
         Part<Real>& q = Q.q;
         q.e = int(tg >> 8);
         q.v = int(tg & 0xFFu);
-        if (q.e != S.e) {
-            S.flush(P, bt, e_base);
-            S.e = q.e;
-        }
+        S.e = q.e;
         q.kx = static_cast<const Real*>(P.kx)[p];
         q.ky = static_cast<const Real*>(P.ky)[p];
         q.kz = static_cast<const Real*>(P.kz)[p];
@@ -719,7 +757,7 @@ __global__ void __launch_bounds__(256, 3)
         P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
         if (NW && count_charge && live) agg_add_i(P.charge, q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z));
     }
-    S.flush(P, bt, e_base);
+    S.flush_warp(P, bt, e_base, true);
     __syncthreads();
     flush_window(P, bt);
 }

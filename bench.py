@@ -154,6 +154,21 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_over_ranks(world: int, times: list, counts: list, device=None) -> tuple[list, list]:
+    """Whole-job figures of a weak-scaling run: the slowest rank's times
+    (max) and the units all ranks processed (sum).  Counts travel as int64,
+    so event totals stay exact."""
+    if world <= 1:
+        return list(times), [int(c) for c in counts]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([int(x) for x in counts], dtype=torch.int64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [int(x) for x in c.tolist()]
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(n_particles: int, steps: int, min_seconds: float = 0.0) -> dict:
     """The FP64 oracle as it stands, single thread, on one bias point of the
@@ -348,13 +363,7 @@ def run_emc(args, world: int, rank: int, local: int):
     d2h = E * 128 + heat.nbytes + cross.nbytes
 
     # ---- reduce over ranks (max time, summed events)
-    if world > 1:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        s = torch.tensor([real, selfe, psteps, ev2], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(s, op=torch.distributed.ReduceOp.SUM)
-        ms, e2e_s = float(t[0]), float(t[1])
-        real, selfe, psteps, ev2 = (int(x) for x in s.tolist())
+    (ms, e2e_s), (real, selfe, psteps, ev2) = reduce_over_ranks(world, [ms, e2e_s], [real, selfe, psteps, ev2], dev)
     ctx.close()
     if rank != 0:
         return

@@ -282,6 +282,51 @@ def electrothermal_comparison(args, stream) -> dict:
     return res
 
 
+# ------------------------------------------------- many-ensemble mixed batch
+def batched_mixed(args, stream) -> dict:
+    """Throughput on the 256-ensemble mixed batch (N ~ 10^U(4, 6), |E| ~
+    U(0, 400) kV/cm, T ~ U(300, 600) K, N_d ~ 10^U(16, 19) cm^-3, 192 bulk +
+    64 nanowire, 5.5e7 electrons): one context per geometry on the bench
+    stream, one step = 10 fs of every ensemble, CUDA-event timed."""
+    import torch
+    import paper_1707_09073_gb300 as emc
+    cfgs = W.config_batched()
+    groups = W.by_geometry(cfgs)
+    ctxs = [emc.Context([cfgs[i] for i in idx], stream=stream.cuda_stream) for _, idx in sorted(groups.items())]
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                for ctx in ctxs:
+                    ctx.emc_step(STEPS_PER_POISSON)
+            for ctx in ctxs:
+                ctx.emc_tally(emc.TALLY_OBS, reset=True)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(args.batched_steps):
+                for ctx in ctxs:
+                    ctx.emc_step(STEPS_PER_POISSON)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            real = sum(int(ctx.emc_tally(emc.TALLY_EVENTS).sum()) for ctx in ctxs)
+            obs = [o for ctx in ctxs for o in ctx.emc_tally(emc.TALLY_OBS)]
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+    selfe = sum(int(o["self_events"].sum()) for o in obs)
+    psteps = sum(int(o["n_samples"]) for o in obs)
+    return {
+        "workload": "256 independent ensembles: N ~ 10^U(4,6) (sum %d), |E| ~ U(0,400) kV/cm, T ~ U(300,600) K, "
+                    "N_d ~ 10^U(16,19) cm^-3; 192 bulk (field along c) + 64 half nanowires (V_d = |E| x 1 um, "
+                    "Poisson every 10 fs); one context per geometry" % sum(c["n_particles"] for c in cfgs),
+        "steps": args.batched_steps, "ms_per_step": ms / args.batched_steps,
+        "events_per_s": real / (ms * 1e-3), "events_incl_self_per_s": (real + selfe) / (ms * 1e-3),
+        "particle_steps_per_s": psteps / (ms * 1e-3),
+    }
+
+
 # --------------------------------------------------------------------- GPU
 def run_emc(args, world: int, rank: int, local: int):
     import numpy as np
@@ -394,6 +439,11 @@ def run_emc(args, world: int, rank: int, local: int):
                "sample": "FP64 oracle, single thread: 1 of the 21 bias points (V_d = 10 V), %d superparticles, "
                          "%d Poisson periods (%.1f s)" % (s["n_particles"], s["periods"], s["seconds"])}
 
+    mixed = None
+    if world == 1 and not args.no_batched:
+        torch.cuda.synchronize(dev)
+        mixed = batched_mixed(args, stream)
+
     et = None
     if world == 1 and not args.no_electrothermal:
         torch.cuda.synchronize(dev)
@@ -415,6 +465,7 @@ def run_emc(args, world: int, rank: int, local: int):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
                    "samples": clocks["samples"]},
         "gpu_launches": launches,
+        "batched_mixed": mixed,
         "surrogate_vs_plain_mc": et,
     }
     print(json.dumps(line), flush=True)
@@ -436,6 +487,8 @@ def main():
     ap.add_argument("--sort-period", type=int, default=0, help="sort particles every this many launches (0 = never)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--no-electrothermal", action="store_true", help="skip the surrogate vs plain-MC comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-ensemble mixed batch")
+    ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
     ap.add_argument("--sur-samples", type=int, default=8192)

@@ -10,6 +10,9 @@
 // real rates); the subcells count electrons for the Poisson update and the
 // net energy handed to phonons.
 #pragma once
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace emc {
@@ -1004,12 +1007,26 @@ size_t flight_smem_bytes(int nb_smem, int n_tab_s)
            (((size_t)n_tab_s * sizeof(Phys<Real>) + 15) & ~size_t(15)) + sizeof(BlockTally);
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel on the
+// current device, shared by every context: it is only ever raised (to the
+// largest request seen on the device), so a context that needs less never
+// lowers the limit under another one that is still alive.
 template <typename Real>
 cudaError_t flight_set_smem(size_t bytes)
 {
-    cudaError_t a = cudaFuncSetAttribute(k_flight<Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static std::mutex mu;
+    static std::map<int, size_t> raised;
+    int dev = 0;
+    cudaError_t a = cudaGetDevice(&dev);
     if (a != cudaSuccess) return a;
-    return cudaFuncSetAttribute(k_flight<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = raised[dev];
+    if (bytes <= cur) return cudaSuccess;
+    a = cudaFuncSetAttribute(k_flight<Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (a != cudaSuccess) return a;
+    a = cudaFuncSetAttribute(k_flight<Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (a == cudaSuccess) cur = bytes;
+    return a;
 }
 
 // resident flight blocks per SM for this shared-memory size

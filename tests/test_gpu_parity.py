@@ -302,3 +302,20 @@ def test_subcell_temperature_fp64_bit_exact(emc, oracle_mod):
     assert np.array_equal(g["crossings"], rt["crossings"])
     assert np.array_equal(g["charge"], rt["charge"])
     assert C == g["charge"].size
+
+
+def test_live_contexts_with_different_shared_memory(emc):
+    """A context whose flight launch needs more shared memory (one table set,
+    staged table) keeps working after a second context that needs less (two
+    table sets, nothing staged) was created on the same device."""
+    big = emc.Context(W.bulk(n_particles=2000, seed=1))
+    try:
+        small = emc.Context([W.bulk(n_particles=1000, T=300.0 + 50.0 * i, seed=2 + i) for i in range(2)])
+        try:
+            small.emc_step(5)
+            big.emc_step(5)
+            assert big.emc_tally(emc.TALLY_OBS)[0]["n_samples"] == 2000 * 5
+        finally:
+            small.close()
+    finally:
+        big.close()

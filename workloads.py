@@ -13,6 +13,7 @@ otherwise (``*_eV``, ``*_per_eV``).
 from __future__ import annotations
 
 import copy
+import random
 
 # --- Table I: parameters for bulk GaN in the electron MC -------------------
 # Valley order: Gamma1, U, Gamma3 (the three lowest conduction valleys).
@@ -147,6 +148,36 @@ def config_nanowire_sweep() -> list[dict]:
 def config_bulk_large(n_particles: int = 10_000_000) -> dict:
     """Precision variant: the bulk physics with 1e7 electrons, 20 ps."""
     return bulk(n_particles=n_particles)
+
+
+def config_batched(n_ens: int = 256, seed: int = 0, scale: float = 1.0) -> list[dict]:
+    """Many independent ensembles in one batch: per ensemble N ~ 10^U(4, 6)
+    electrons (times `scale`, at least 1), |E| ~ U(0, 400) kV/cm, T ~ U(300,
+    600) K, N_d ~ 10^U(16, 19) cm^-3; every fourth ensemble is a half nanowire
+    with V_d = |E| L (Poisson field), the others bulk with the field along c.
+    Draws come from Python's Mersenne Twister seeded with `seed`, in ensemble
+    order (N, |E|, T, N_d)."""
+    rng = random.Random(seed)
+    out = []
+    for e in range(n_ens):
+        n = max(1, int(round(10.0 ** rng.uniform(4.0, 6.0) * scale)))
+        E = rng.uniform(0.0, 4.0e7)
+        T = rng.uniform(300.0, 600.0)
+        nd = 10.0 ** rng.uniform(16.0, 19.0)
+        s = 1_000_000 * seed + e
+        if e % 4 == 3:
+            out.append(nanowire(n_particles=n, Vd=E * 1.0e-6, T=T, Nd_cm3=nd, seed=s))
+        else:
+            out.append(bulk(n_particles=n, field_V_m=E, T=T, Nd_cm3=nd, seed=s))
+    return out
+
+
+def by_geometry(cfgs: list[dict]) -> dict[int, list[int]]:
+    """Indices of the configurations of each geometry (one context each)."""
+    g: dict[int, list[int]] = {}
+    for i, c in enumerate(cfgs):
+        g.setdefault(int(c["geometry"]), []).append(i)
+    return g
 
 
 def copy_config(c: dict, **over) -> dict:

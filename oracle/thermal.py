@@ -7,6 +7,11 @@ term v_g / L_b (the size-modified mean free paths of the paragraph after
 Eq. (3)):  kappa = 3 * (1/3) int_0^q0 C(q) v_g(q)^2 tau(q) q^2 / (2 pi^2) dq,
 C(q) = hbar omega dn/dT.
 
+Phonon-electron scattering in doped wires (Eq. (1)): an extra rate
+tau_E^-1(omega) from the deformation-potential coupling of acoustic phonons
+to the free electrons, with the Fermi level of n_e electrons in a parabolic
+band of DOS mass m* at the lattice temperature (full ionization).
+
 Fourier problem on the subcell grid: sum over faces g_f (T_c - T_n) +
 boundary terms g_b (T_c - T_sink) = q_c, g_f = harmonic-mean kappa / h^2;
 contact faces (x = 0, x = L) at T_sink half a cell away; the bottom face
@@ -15,15 +20,64 @@ faces adiabatic.  kappa(T) by Picard iteration.
 """
 import numpy as np
 from scipy import constants as sc
-from scipy import integrate, sparse
+from scipy import integrate, optimize, sparse
 from scipy.sparse import linalg as spla
 
 HB, KB = sc.hbar, sc.k
 
 
-def kappa(T, mat, L_b=0.0):
+def fermi_half(eta):
+    """Normalised Fermi-Dirac integral of order 1/2:
+    (2/sqrt(pi)) int_0^inf sqrt(x) / (1 + exp(x - eta)) dx."""
+    f = lambda x: np.sqrt(x) * np.exp(-np.logaddexp(0.0, x - eta))
+    top = max(eta, 0.0) + 80.0
+    return 2.0 / np.sqrt(np.pi) * integrate.quad(f, 0.0, top, epsabs=0, epsrel=1e-13, limit=400)[0]
+
+
+def band_density(T, m_rel):
+    """Effective density of states 2 (m* k T / 2 pi hbar^2)^(3/2), m^-3."""
+    return 2.0 * (m_rel * sc.m_e * KB * T / (2.0 * np.pi * HB ** 2)) ** 1.5
+
+
+def fermi_level(n, T, m_rel):
+    """E_F (J, from the band edge) with n = N_c F_1/2(E_F / kT)."""
+    Nc = band_density(T, m_rel)
+    eta = optimize.brentq(lambda e: np.log(fermi_half(e)) - np.log(n / Nc), -200.0, 400.0, xtol=1e-13, rtol=1e-14)
+    return eta * KB * T
+
+
+def tau_e_inv(w, T, n, elec, E_F=None):
+    """Phonon-electron scattering rate of Eq. (1) (1/s) for phonons of
+    angular frequency w; elec: m_rel (DOS mass), Da_eV, rho_kg_m3, vg_m_s
+    (the averaged phonon group velocity)."""
+    m = elec["m_rel"] * sc.m_e
+    Da = elec["Da_eV"] * sc.e
+    v = elec["vg_m_s"]
+    kT = KB * T
+    if E_F is None:
+        E_F = fermi_level(n, T, elec["m_rel"])
+    half = 0.5 * m * v * v
+    pre = Da ** 2 * m ** 3 * v / (4.0 * np.pi * HB ** 4 * elec["rho_kg_m3"]) * kT / half
+    a = (half - E_F) / kT + (HB * w) ** 2 / (8.0 * m * v * v * kT)
+    y = HB * w / (2.0 * kT)
+    # braces of Eq. (1): hbar w / kT - ln[(1 + e^(a+y)) / (1 + e^(a-y))], with
+    # hbar w / kT = 2y.  Written with ln(1 + e^z) = max(z, 0) + ln(1 + e^-|z|)
+    # the 2y cancels exactly against the max parts, which keeps the small
+    # non-degenerate values (a >> 1) free of cancellation.
+    sp = lambda z: np.log1p(np.exp(-abs(z)))
+    if a - y >= 0.0:
+        br = sp(a - y) - sp(a + y)
+    elif a + y <= 0.0:
+        br = 2.0 * y - sp(a + y) + sp(a - y)
+    else:
+        br = (y - a) - sp(a + y) + sp(a - y)
+    return pre * br
+
+
+def kappa(T, mat, L_b=0.0, n_e=0.0, elec=None):
     q0, wm = mat["k0_per_m"], mat["omega_max_rad_s"]
     A, B1, B2 = mat["A_s3"], mat["B1_s_per_K"], mat["B2_K"]
+    E_F = fermi_level(n_e, T, elec["m_rel"]) if n_e > 0 else None
 
     def f(q):
         w = wm * np.sin(np.pi * q / (2 * q0))
@@ -33,6 +87,8 @@ def kappa(T, mat, L_b=0.0):
         rate = A * w ** 4 + B1 * w ** 2 * T * np.exp(-B2 / T)
         if L_b > 0:
             rate = rate + vg / L_b
+        if E_F is not None:
+            rate = rate + tau_e_inv(w, T, n_e, elec, E_F)
         return HB * w * dndT * vg * vg / rate * q * q / (2 * np.pi ** 2)
 
     return integrate.quad(f, 0.0, q0, epsabs=0, epsrel=1e-10, limit=400)[0]
@@ -71,14 +127,14 @@ def operator(cfg, kap, T_sink, h_bottom):
     return A, rhs_b
 
 
-def solve(cfg, q, mat, T_sink=300.0, h_bottom=1e9, L_b=0.0, tol=1e-8, max_picard=50, T0=None):
+def solve(cfg, q, mat, T_sink=300.0, h_bottom=1e9, L_b=0.0, tol=1e-8, max_picard=50, T0=None, n_e=0.0, elec=None):
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
     T = np.full(n, T_sink) if T0 is None else np.array(T0, dtype=float)
     cache = {}
     def kap_of(t):
         key = round(float(t), 9)
         if key not in cache:
-            cache[key] = kappa(t, mat, L_b)
+            cache[key] = kappa(t, mat, L_b, n_e, elec)
         return cache[key]
     for _ in range(max_picard):
         kap = np.array([kap_of(t) for t in T])

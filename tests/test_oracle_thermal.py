@@ -60,3 +60,53 @@ def test_one_dimensional_closed_form():
     want = 300.0 + q[0] * x * (L - x) / (2 * k) + q[0] * h * h / (8 * k)
     got = T.reshape(c["nx"], -1)[:, 0]
     assert np.allclose(got - 300.0, want - 300.0, rtol=2e-3)
+
+
+# ---- phonon-electron scattering, Eq. (1)
+def test_fermi_half_closed_form_at_zero():
+    # F_1/2(0) = (1 - 2^(-1/2)) zeta(3/2)
+    from scipy.special import zeta
+    assert thermal.fermi_half(0.0) == pytest.approx((1 - 2 ** -0.5) * zeta(1.5), rel=1e-10)
+
+
+def test_fermi_level_limits():
+    m = W.ELECTRON_PHONON_GAN["m_rel"]
+    # non-degenerate: n = N_c exp(E_F / kT)
+    n = 1e18
+    Nc = 2.0 * (m * 9.1093837015e-31 * 1.380649e-23 * 300.0 / (2 * np.pi * 1.054571817e-34 ** 2)) ** 1.5
+    assert thermal.fermi_level(n, 300.0, m) == pytest.approx(1.380649e-23 * 300.0 * np.log(n / Nc), rel=1e-9)
+    # degenerate (T -> 0): E_F = hbar^2 (3 pi^2 n)^(2/3) / 2 m*
+    n = 1e26
+    ef0 = 1.054571817e-34 ** 2 * (3 * np.pi ** 2 * n) ** (2 / 3) / (2 * m * 9.1093837015e-31)
+    assert thermal.fermi_level(n, 20.0, m) == pytest.approx(ef0, rel=1e-4)
+
+
+def test_tau_e_non_degenerate_limit():
+    # for E_F far below the band edge the braces of Eq. (1) reduce to
+    # exp(-(m v^2/2 - E_F)/kT - (hbar w)^2 / 8 m v^2 kT) * 2 sinh(hbar w / 2kT),
+    # and exp(E_F / kT) = n / N_c
+    el = W.ELECTRON_PHONON_GAN
+    kB, hb, me, e = 1.380649e-23, 1.054571817e-34, 9.1093837015e-31, 1.602176634e-19
+    T, n = 300.0, 1e16
+    m, v = el["m_rel"] * me, el["vg_m_s"]
+    Nc = 2.0 * (m * kB * T / (2 * np.pi * hb ** 2)) ** 1.5
+    half = 0.5 * m * v * v
+    pre = (el["Da_eV"] * e) ** 2 * m ** 3 * v / (4 * np.pi * hb ** 4 * el["rho_kg_m3"]) * kB * T / half
+    for w in (1e11, 1e12, 3e12):
+        want = pre * (n / Nc) * np.exp(-half / (kB * T) - (hb * w) ** 2 / (8 * m * v * v * kB * T)) \
+            * 2 * np.sinh(hb * w / (2 * kB * T))
+        assert thermal.tau_e_inv(w, T, n, el) == pytest.approx(want, rel=1e-6)
+
+
+def test_electron_scattering_kappa_reduction():
+    # the paper: free electrons reduce the room-temperature conductivity of
+    # Si-doped GaN by ~13% at 7.0e18 cm^-3 (its ref. [16]); this reading of
+    # Eq. (1) gives 16%
+    el = W.ELECTRON_PHONON_GAN
+    k0 = thermal.kappa(300.0, W.TABLE_II_GAN)
+    k7 = thermal.kappa(300.0, W.TABLE_II_GAN, n_e=7e24, elec=el)
+    assert 0.10 < 1.0 - k7 / k0 < 0.20
+    # more electrons scatter more; no electrons, no change
+    k1 = thermal.kappa(300.0, W.TABLE_II_GAN, n_e=1e24, elec=el)
+    assert k7 < k1 < k0
+    assert thermal.kappa(300.0, W.TABLE_II_GAN, n_e=0.0, elec=el) == k0

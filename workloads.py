@@ -38,6 +38,15 @@ TABLE_II_GAN = {
     "B1_s_per_K": 1.10e-19,
     "B2_K": 200.0,
 }
+# Phonon-electron scattering of Eq. (1): DOS mass of the Gamma1 valley and
+# D_a, rho from Table I; the averaged phonon group velocity is the averaged
+# sound velocity the text quotes for GaN (3338 m/s)
+ELECTRON_PHONON_GAN = {
+    "m_rel": 0.21,
+    "Da_eV": 8.3,
+    "rho_kg_m3": 6095.0,
+    "vg_m_s": 3338.0,
+}
 TABLE_II_SIC = {
     "k0_per_m": 8.94e9,
     "omega_max_rad_s": 7.12e13,

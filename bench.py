@@ -241,7 +241,10 @@ def electrothermal_comparison(args, stream) -> dict:
     t_train = time.perf_counter() - t0
     nb = args.et_biases
     cfgs = [W.nanowire(n_particles=args.et_particles, Vd=20.0 * i / (nb - 1), seed=500 + i) for i in range(nb)]
-    tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=args.h_bottom, L_boundary=120e-9, tol_K=1e-3)
+    # kappa(T) with the phonon-electron scattering of Eq. (1) at the wire's
+    # doping (1e18 cm^-3)
+    tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=args.h_bottom, L_boundary=120e-9, tol_K=1e-3,
+                                n_e=cfgs[0]["Nd"], elec=W.ELECTRON_PHONON_GAN)
     out = {}
     for mode in ("plain", "surrogate"):
         ctx = emc.Context(cfgs, stream=stream.cuda_stream)
@@ -254,6 +257,18 @@ def electrothermal_comparison(args, stream) -> dict:
             else:
                 r = ET.surrogate_accelerated(ctx, sur, tc, max_iter=15, rtol=0.01)
                 t_sur = r["surrogate_seconds"]
+            if mode == "plain":
+                # Fig. 5 quantity: peak rise / emitted phonon power; half wire
+                # as simulated, and the 31-wire array of identical wires
+                # (each full wire emits twice the half wire's power)
+                pts = []
+                for i in range(0, nb, max(1, (nb - 1) // 8)):
+                    R = float(r["R_th_K_per_W"][i])
+                    if R == R:
+                        pts.append({"Vd": cfgs[i]["Vd"], "peak_rise_K": float(r["peak"][i]),
+                                    "power_W_half_wire": float(r["power_W"][i]), "R_th_K_per_W_half_wire": R,
+                                    "R_th_K_per_W_array31": R / (2.0 * 31.0)})
+                out["R_th_vs_Vd"] = pts
             out[mode] = {"converged": r["converged"], "mc_iterations": r["iterations"],
                          "seconds": time.perf_counter() - t0, "surrogate_seconds": t_sur,
                          "peak_rise_K_max_bias": float(r["peak"][-1]),
@@ -267,12 +282,14 @@ def electrothermal_comparison(args, stream) -> dict:
     hot = out["plain"]["peak"] > 1.0
     res = {
         "workload": "half nanowire 3x6x100, %d drain biases 0..20 V x %d superparticles, Fourier with kappa(T) "
-                    "(Table II, 120 nm boundary), h_bottom %.1e W/m2/K; converged when every peak rise changes "
+                    "(Table II, 120 nm boundary, phonon-electron scattering of Eq. (1) at 1e18 cm^-3), "
+                    "h_bottom %.1e W/m2/K; converged when every peak rise changes "
                     "< max(1%%, 0.5 K) between iterations; surrogate run: Monte Carlo iteration 1 at 300 K, then the "
                     "surrogate's current-vs-temperature response jumps to a predicted self-consistent field, then "
                     "Monte Carlo iterations until stationary" % (nb, args.et_particles, args.h_bottom),
         "plain_mc": {k: v for k, v in out["plain"].items() if k != "peak"},
         "surrogate_warm_start": {k: v for k, v in out["surrogate"].items() if k != "peak"},
+        "R_th_vs_Vd": out.get("R_th_vs_Vd"),
         "speedup": out["plain"]["seconds"] / max(out["surrogate"]["seconds"], 1e-9),
         "peak_rise_max_rel_diff": float(np.max(np.abs(dp[hot]) / out["plain"]["peak"][hot])) if hot.any() else None,
         "peak_rise_rel_diff_max_bias": float(abs(dp[-1]) / max(out["plain"]["peak"][-1], 1e-9)),

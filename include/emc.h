@@ -284,6 +284,11 @@ typedef struct emc_thermal_config {
     double L_boundary;      /* m, boundary-scattering length (0: bulk) */
     double tol_K;           /* Picard stop: max |T_new - T_old| */
     double k0_per_m, omega_max_rad_s, A_s3, B1_s_per_K, B2_K;  /* Table II column */
+    /* phonon-electron scattering of Eq. (1), off when n_e_m3 = 0: free
+     * electron density (m^-3), their DOS mass / m0, acoustic deformation
+     * potential (eV), mass density (kg/m^3), averaged phonon group velocity
+     * (m/s); the Fermi level follows from n_e at each temperature */
+    double n_e_m3, m_e_rel, Da_eV, rho_kg_m3, vg_e_m_s;
     int32_t max_picard, max_cg;
 } emc_thermal_config;
 

@@ -17,7 +17,6 @@
 #include <map>
 #include <mutex>
 #include <string>
-#include <tuple>
 #include <vector>
 
 #include "../../include/emc.h"
@@ -39,8 +38,82 @@ constexpr double kTLo = 150.0, kTStep = 0.5;
 constexpr int kNT = 2701;  // 150 .. 1500 K
 constexpr int kMaxThermalCells = 2048;
 
+// Normalised Fermi-Dirac integral of order 1/2, F(eta) = (2/sqrt(pi))
+// int_0^inf sqrt(x) / (1 + e^(x - eta)) dx, with x = t^2 and the midpoint
+// rule in t; dF/deta (the order -1/2 integral) from the same points.
+void fermi_half(double eta, double* F, double* dF)
+{
+    const int n = 1200;
+    const double tmax = std::sqrt(std::fmax(eta, 0.0) + 80.0), h = tmax / n;
+    double acc = 0.0, dacc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double t = (i + 0.5) * h, z = t * t - eta;
+        const double occ = z > 0.0 ? std::exp(-z) / (1.0 + std::exp(-z)) : 1.0 / (1.0 + std::exp(z));
+        acc += 2.0 * t * t * occ;
+        dacc += 2.0 * t * t * occ * (1.0 - occ);
+    }
+    *F = acc * h * 2.0 / std::sqrt(kPi);
+    *dF = dacc * h * 2.0 / std::sqrt(kPi);
+}
+
+// Fermi level (J from the band edge) of n electrons per m^3 in a parabolic
+// band of DOS mass m_rel m0 at T: n = N_c F_1/2(E_F / kT).  Newton on
+// ln F(eta) from the non-degenerate or degenerate limit, kept inside a
+// shrinking bracket (bisection when a step leaves it).
+double fermi_level(double n, double T, double m_rel)
+{
+    const double Nc = 2.0 * std::pow(m_rel * kM0 * kKB * T / (2.0 * kPi * kHbar * kHbar), 1.5);
+    const double target = std::log(n / Nc);
+    double lo = -200.0, hi = 400.0;
+    double eta = target < 0.0 ? target : std::pow(0.75 * std::sqrt(kPi) * std::exp(target), 2.0 / 3.0);
+    eta = std::fmin(std::fmax(eta, lo), hi);
+    for (int it = 0; it < 200; ++it) {
+        double F, dF;
+        fermi_half(eta, &F, &dF);
+        const double g = std::log(F) - target;
+        if (g < 0.0) lo = eta;
+        else hi = eta;
+        double next = eta - g * F / dF;
+        if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+        if (std::fabs(next - eta) < 1e-13 * (1.0 + std::fabs(eta))) {
+            eta = next;
+            break;
+        }
+        eta = next;
+    }
+    return eta * kKB * T;
+}
+
+// Phonon-electron scattering rate of Eq. (1) (1/s).  The braces
+// hbar w / kT - ln[(1 + e^(a+y)) / (1 + e^(a-y))] (hbar w / kT = 2y) are
+// evaluated with ln(1 + e^z) = max(z, 0) + ln(1 + e^-|z|), the 2y cancelling
+// exactly, so non-degenerate values (a >> 1) keep their precision.
+double tau_e_inv(double w, double T, double E_F, const emc_thermal_config& tc)
+{
+    const double m = tc.m_e_rel * kM0, v = tc.vg_e_m_s, kT = kKB * T;
+    const double Da = tc.Da_eV * kQ;
+    const double half = 0.5 * m * v * v;
+    const double pre = Da * Da * m * m * m * v / (4.0 * kPi * kHbar * kHbar * kHbar * kHbar * tc.rho_kg_m3) * kT / half;
+    const double a = (half - E_F) / kT + (kHbar * w) * (kHbar * w) / (8.0 * m * v * v * kT);
+    const double y = kHbar * w / (2.0 * kT);
+    auto sp = [](double z) { return std::log1p(std::exp(-std::fabs(z))); };
+    double br;
+    if (a - y >= 0.0) br = sp(a - y) - sp(a + y);
+    else if (a + y <= 0.0) br = 2.0 * y - sp(a + y) + sp(a - y);
+    else br = (y - a) - sp(a + y) + sp(a - y);
+    return pre * br;
+}
+
+// the phonon-electron parameters are either off (n_e = 0) or all positive
+bool electrons_ok(const emc_thermal_config& tc)
+{
+    if (tc.n_e_m3 == 0.0) return true;
+    return tc.n_e_m3 > 0.0 && tc.m_e_rel > 0.0 && tc.Da_eV > 0.0 && tc.rho_kg_m3 > 0.0 && tc.vg_e_m_s > 0.0;
+}
+
 // kappa(T) of the GaN column of Table II on the grid above (midpoint rule in
-// the wave vector, 4000 points)
+// the wave vector, 4000 points), with the boundary term and, when n_e > 0,
+// the phonon-electron term of Eq. (1)
 std::vector<double> kappa_table_build(const emc_thermal_config& tc)
 {
     const double q0 = tc.k0_per_m, wm = tc.omega_max_rad_s;
@@ -48,6 +121,7 @@ std::vector<double> kappa_table_build(const emc_thermal_config& tc)
     const int nq = 4000;
     for (int t = 0; t < kNT; ++t) {
         const double T = kTLo + kTStep * t;
+        const double E_F = tc.n_e_m3 > 0.0 ? fermi_level(tc.n_e_m3, T, tc.m_e_rel) : 0.0;
         double acc = 0.0;
         for (int i = 0; i < nq; ++i) {
             const double q = (i + 0.5) * q0 / nq;
@@ -58,6 +132,7 @@ std::vector<double> kappa_table_build(const emc_thermal_config& tc)
             const double dndT = x * std::exp(x) / (em1 * em1) / T;
             double rate = tc.A_s3 * w * w * w * w + tc.B1_s_per_K * w * w * T * std::exp(-tc.B2_K / T);
             if (tc.L_boundary > 0.0) rate += vg / tc.L_boundary;
+            if (tc.n_e_m3 > 0.0) rate += tau_e_inv(w, T, E_F, tc);
             acc += kHbar * w * dndT * vg * vg / rate * q * q / (2.0 * kPi * kPi);
         }
         out[t] = acc * q0 / nq;
@@ -69,8 +144,9 @@ std::vector<double> kappa_table_build(const emc_thermal_config& tc)
 std::vector<double> kappa_table(const emc_thermal_config& tc)
 {
     static std::mutex mu;
-    static std::map<std::tuple<double, double, double, double, double, double>, std::vector<double>> cache;
-    const auto key = std::make_tuple(tc.k0_per_m, tc.omega_max_rad_s, tc.A_s3, tc.B1_s_per_K, tc.B2_K, tc.L_boundary);
+    static std::map<std::vector<double>, std::vector<double>> cache;
+    const std::vector<double> key = {tc.k0_per_m, tc.omega_max_rad_s, tc.A_s3, tc.B1_s_per_K, tc.B2_K, tc.L_boundary,
+                                     tc.n_e_m3, tc.m_e_rel, tc.Da_eV, tc.rho_kg_m3, tc.vg_e_m_s};
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it == cache.end()) it = cache.emplace(key, kappa_table_build(tc)).first;
@@ -224,7 +300,7 @@ extern "C" {
 
 emc_status emc_kappa(const emc_thermal_config* tc, const double* T, double* kappa, int32_t n)
 {
-    if (!tc || n < 0 || (n > 0 && (!T || !kappa))) return EMC_EINVAL;
+    if (!tc || n < 0 || (n > 0 && (!T || !kappa)) || !electrons_ok(*tc)) return EMC_EINVAL;
     const std::vector<double> tab = kappa_table(*tc);
     for (int i = 0; i < n; ++i) {
         double f = (T[i] - kTLo) / kTStep;
@@ -245,7 +321,7 @@ emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const d
         return ctx_fail(ctx, EMC_ESTATE, "emc_thermal_solve needs the nanowire geometry");
     const int n = nx * ny * nz;
     if (n > kMaxThermalCells) return ctx_fail(ctx, EMC_EINVAL, "emc_thermal_solve: at most 2048 subcells");
-    if (!(tc->T_sink > 0) || !(tc->h_bottom > 0) || tc->max_picard <= 0 || tc->max_cg <= 0)
+    if (!(tc->T_sink > 0) || !(tc->h_bottom > 0) || tc->max_picard <= 0 || tc->max_cg <= 0 || !electrons_ok(*tc))
         return ctx_fail(ctx, EMC_EINVAL, "emc_thermal_solve: invalid configuration");
     cudaStream_t st = ctx_stream(ctx);
     const std::vector<double> tab = kappa_table(*tc);

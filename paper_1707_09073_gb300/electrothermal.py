@@ -45,6 +45,22 @@ def peak_rise(T: np.ndarray, T_sink: float) -> np.ndarray:
     return T.max(axis=1) - T_sink
 
 
+def emitted_power(ctx, q: np.ndarray) -> np.ndarray:
+    """Net power handed to phonons (W) per ensemble from a heat map (W/m^3)."""
+    c = ctx.cfgs[0]
+    return q.sum(axis=1) * (c["Lx"] * c["Ly"] * c["Lz"] / ctx.n_cell)
+
+
+def thermal_resistance(T: np.ndarray, power: np.ndarray, T_sink: float) -> np.ndarray:
+    """Device thermal resistance as the paper defines it for Fig. 5: the
+    largest temperature rise divided by the total energy rate of the phonons
+    the electrons emit (counted by the Monte Carlo, not the Joule heat).  K/W,
+    per ensemble; NaN where no power is emitted."""
+    rise = T.max(axis=1) - T_sink
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(power > 0, rise / power, np.nan)
+
+
 def iterate(ctx, tc, T0: np.ndarray, warm_steps: int = 300, avg_steps: int = 1000, max_iter: int = 12,
             rtol: float = 0.01, atol: float = 0.5, relax: float = 1.0, prev_peak=None) -> dict:
     """Monte Carlo <-> Fourier fixed point from T0; converged when the peak
@@ -62,11 +78,13 @@ def iterate(ctx, tc, T0: np.ndarray, warm_steps: int = 300, avg_steps: int = 100
         pk = peak_rise(T, tc.T_sink)
         hist.append(pk.copy())
         if prev is not None and abs(pk.max() - prev.max()) <= max(rtol * abs(pk.max()), atol):
-            return {"converged": True, "iterations": it, "T": T, "peak": pk, "history": hist,
-                    "seconds": time.perf_counter() - t0}
+            P = emitted_power(ctx, q)
+            return {"converged": True, "iterations": it, "T": T, "peak": pk, "history": hist, "power_W": P,
+                    "R_th_K_per_W": thermal_resistance(T, P, tc.T_sink), "seconds": time.perf_counter() - t0}
         prev = pk
+    P = emitted_power(ctx, q)
     return {"converged": False, "iterations": max_iter, "T": T, "peak": peak_rise(T, tc.T_sink), "history": hist,
-            "seconds": time.perf_counter() - t0}
+            "power_W": P, "R_th_K_per_W": thermal_resistance(T, P, tc.T_sink), "seconds": time.perf_counter() - t0}
 
 
 def _invert(v: np.ndarray, Eg: np.ndarray, target: np.ndarray) -> np.ndarray:

@@ -284,15 +284,24 @@ def obs_dict(o: EmcObs) -> dict:
 class EmcThermalConfig(C.Structure):
     _fields_ = [("T_sink", C.c_double), ("h_bottom", C.c_double), ("L_boundary", C.c_double), ("tol_K", C.c_double),
                 ("k0_per_m", C.c_double), ("omega_max_rad_s", C.c_double), ("A_s3", C.c_double),
-                ("B1_s_per_K", C.c_double), ("B2_K", C.c_double), ("max_picard", C.c_int32), ("max_cg", C.c_int32)]
+                ("B1_s_per_K", C.c_double), ("B2_K", C.c_double),
+                ("n_e_m3", C.c_double), ("m_e_rel", C.c_double), ("Da_eV", C.c_double), ("rho_kg_m3", C.c_double),
+                ("vg_e_m_s", C.c_double), ("max_picard", C.c_int32), ("max_cg", C.c_int32)]
 
 
 def thermal_config(table_ii: dict, T_sink=300.0, h_bottom=1e9, L_boundary=120e-9, tol_K=1e-6, max_picard=50,
-                   max_cg=5000) -> EmcThermalConfig:
+                   max_cg=5000, n_e=0.0, elec: dict | None = None) -> EmcThermalConfig:
+    """Thermal-side parameters; n_e (m^-3) > 0 with elec = {m_rel, Da_eV,
+    rho_kg_m3, vg_m_s} adds the phonon-electron scattering of Eq. (1)."""
     t = EmcThermalConfig()
     t.T_sink, t.h_bottom, t.L_boundary, t.tol_K = T_sink, h_bottom, L_boundary, tol_K
     t.k0_per_m, t.omega_max_rad_s = table_ii["k0_per_m"], table_ii["omega_max_rad_s"]
     t.A_s3, t.B1_s_per_K, t.B2_K = table_ii["A_s3"], table_ii["B1_s_per_K"], table_ii["B2_K"]
+    if n_e > 0:
+        if elec is None:
+            raise ValueError("n_e > 0 needs the electron parameters")
+        t.n_e_m3, t.m_e_rel, t.Da_eV = n_e, elec["m_rel"], elec["Da_eV"]
+        t.rho_kg_m3, t.vg_e_m_s = elec["rho_kg_m3"], elec["vg_m_s"]
     t.max_picard, t.max_cg = max_picard, max_cg
     return t
 

@@ -3,9 +3,9 @@
 // velocity, mean energy, valley fractions, heat rate, current density),
 // trained on data the Monte Carlo itself produces.
 //
-// Every matrix product runs on the tensor cores with BF16 operands and FP32
-// accumulation (inline-PTX mma.sync m16n8k16); master weights, gradients and
-// Adam moments are FP32.  Matrices are row-major; a layer holds
+// Every matrix product runs on the 5th-generation tensor cores (tcgen05.mma,
+// BF16 operands staged in shared memory, FP32 accumulator in tensor memory);
+// master weights, gradients and Adam moments are FP32.  Matrices are row-major; a layer holds
 // W [out_p][in_p] and b [out_p] with dimensions padded to multiples of 16;
 // the padding is zero and stays zero (its gradients are zero).
 #include <cuda_bf16.h>
@@ -47,6 +47,7 @@ struct emc_mlp {
     float *da = nullptr, *dzf = nullptr;
     __nv_bfloat16 *dzb = nullptr, *dzT = nullptr, *aT = nullptr;
     float *X = nullptr, *Y = nullptr, *loss = nullptr;
+    int* d_err = nullptr;  // set by a tensor-core wait that expired
     float *Xall = nullptr, *Yall = nullptr;
     int64_t nall = 0;
     int64_t step = 0;
@@ -92,17 +93,6 @@ int pad16(int x) { return (x + 15) / 16 * 16; }
 unsigned gridn(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ------------------------------------------------------------- tensor core
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t ld2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
 __device__ __forceinline__ float silu(float x) { return x / (1.f + __expf(-x)); }
 __device__ __forceinline__ float dsilu(float x)
 {
@@ -112,67 +102,241 @@ __device__ __forceinline__ float dsilu(float x)
 
 enum { EPI_BIAS = 1, EPI_SILU = 2, EPI_ACC = 4 };
 
-// C[M][N] = A[M][K] . B[N][K]^T with bf16 row-major operands and fp32
-// accumulation.  One warp owns a 16-row x 32-column tile (four m16n8k16
-// tiles) and walks K in steps of 16; fragments are read straight from
-// global memory (the matrices here are small).  M % 16 == 0, N % 8 == 0,
-// K % 16 == 0.  Epilogue: + bias[n] (EPI_BIAS); z (fp32) receives the sum
-// (or adds it, EPI_ACC); out (bf16) receives SiLU(sum) (EPI_SILU) or sum.
-__global__ void k_gemm(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B, int M, int N, int K,
-                       const float* __restrict__ bias, int epi, float* z, int ldz, __nv_bfloat16* out, int ldo)
+// 5th-generation tensor cores (tcgen05): one CTA of four warps computes a
+// 128-row x BN-column tile of C = A . B^T (A [M][K], B [N][K], both BF16
+// row-major, i.e. K-major operands) over a range of K, with the FP32
+// accumulator in tensor memory.  K is walked in blocks of 64 through two
+// shared-memory stages: the warps stage block i + 1 (canonical K-major
+// layout without swizzle: 8-row x 16-byte core matrices, 128 B apart along
+// K, 8-row groups 1024 B apart) while the tensor core works on block i; one
+// thread issues the 128 x BN x 16 MMAs and commits each block to the
+// mbarrier of its stage, which the warps wait on before refilling it.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w owns rows 32w ..
+// 32w + 31), adds the bias, applies SiLU and writes FP32 and/or BF16; with
+// K split over several CTAs (gridDim.z > 1) the partial sums are added
+// atomically into z, which the caller has zeroed.  Every wait is bounded:
+// on expiry the error word is set, the MMAs in flight are waited for
+// (bounded again), tensor memory is freed and the CTA exits.
+constexpr int kTcBM = 128, kTcBK = 64;
+constexpr size_t kTcStageA = (size_t)kTcBM * kTcBK * 2;
+constexpr long long kTcWaitCycles = 2000000000ll;  // ~1 s at the GB300 clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int tiles_n = (N + 31) / 32;
-    const int tm = warp / tiles_n, tn = warp % tiles_n;
-    if (tm * 16 >= M) return;
-    const int g = lane >> 2, t = lane & 3;
-    const int r0 = tm * 16, n0 = tn * 32;
-    float c[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a[4];
-        a[0] = ld2(A + (size_t)(r0 + g) * K + k0 + 2 * t);
-        a[1] = ld2(A + (size_t)(r0 + g + 8) * K + k0 + 2 * t);
-        a[2] = ld2(A + (size_t)(r0 + g) * K + k0 + 8 + 2 * t);
-        a[3] = ld2(A + (size_t)(r0 + g + 8) * K + k0 + 8 + 2 * t);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int nn = n0 + 8 * j;
-            if (nn < N) {
-                uint32_t b[2];
-                b[0] = ld2(B + (size_t)(nn + g) * K + k0 + 2 * t);
-                b[1] = ld2(B + (size_t)(nn + g) * K + k0 + 8 + 2 * t);
-                mma_bf16(c[j], a, b);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int nn = n0 + 8 * j;
-        if (nn >= N) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int row = r0 + g + 8 * h;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int col = nn + 2 * t + q;
-                float v = c[j][2 * h + q];
-                if (epi & EPI_BIAS) v += bias[col];
-                if (z) {
-                    float* zz = z + (size_t)row * ldz + col;
-                    *zz = (epi & EPI_ACC) ? *zz + v : v;
-                }
-                if (out) out[(size_t)row * ldo + col] = __float2bfloat16_rn((epi & EPI_SILU) ? silu(v) : v);
-            }
-        }
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kTcWaitCycles) return false;
     }
 }
 
-void gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, const float* bias, int epi, float* z,
-          int ldz, __nv_bfloat16* out, int ldo, cudaStream_t st)
+// stage the K block [k0, k0 + kb) of rows [r0, r0 + rows) of X (row length
+// K) in the core-matrix layout; rows at or beyond rmax are zero
+__device__ __forceinline__ void tc_stage(unsigned char* dst, const __nv_bfloat16* __restrict__ X, int r0, int rows,
+                                         int rmax, int K, int k0, int kb)
 {
-    const int64_t warps = (int64_t)(M / 16) * ((N + 31) / 32);
-    k_gemm<<<gridn(warps * 32, 128), 128, 0, st>>>(A, B, M, N, K, bias, epi, z, ldz, out, ldo);
+    const int nch = kb >> 3;
+    for (int i = threadIdx.x; i < rows * nch; i += blockDim.x) {
+        const int r = i / nch, c = i - (i / nch) * nch;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r0 + r < rmax) v = *reinterpret_cast<const uint4*>(X + (size_t)(r0 + r) * K + k0 + 8 * c);
+        *reinterpret_cast<uint4*>(dst + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
+                                                 int M, int N, int K, int BN, int k_per_cta,
+                                                 const float* __restrict__ bias, int epi, float* z, int ldz,
+                                                 __nv_bfloat16* out, int ldo, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    const size_t stage = kTcStageA + (size_t)BN * kTcBK * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * BN;
+    const int kbeg = blockIdx.z * k_per_cta, kend = min(K, kbeg + k_per_cta);
+    const bool split = gridDim.z > 1;
+    const uint32_t ncols = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc_idesc(kTcBM, BN);
+    uint32_t phase[2] = {0u, 0u};
+    int pending[2] = {0, 0};  // commits of a stage not yet waited for
+    bool ok = true;
+    int it = 0;
+    for (int k0 = kbeg; k0 < kend && ok; k0 += kTcBK, ++it) {
+        const int sidx = it & 1;
+        unsigned char* sA = tc_smem + sidx * stage;
+        unsigned char* sB = sA + kTcStageA;
+        if (pending[sidx]) {
+            // the MMAs that read this stage two blocks ago must be done (on
+            // expiry the commit stays pending and the drain below waits again)
+            ok = __syncthreads_and(mbar_wait(bar0 + 8u * sidx, phase[sidx])) != 0;
+            if (!ok) break;
+            phase[sidx] ^= 1u;
+            pending[sidx] = 0;
+        }
+        const int kb = min(kTcBK, kend - k0);
+        tc_stage(sA, A, m0, kTcBM, M, K, k0, kb);
+        tc_stage(sB, B, n0, BN, N, K, k0, kb);
+        // generic-proxy stores must be visible to the tensor core's reads
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int s = 0; s < (kb >> 4); ++s) {
+                const uint64_t da = tc_sdesc(smem_u32(sA) + 256u * s, 128u, 1024u);
+                const uint64_t db = tc_sdesc(smem_u32(sB) + 256u * s, 128u, 1024u);
+                const uint32_t acc = (k0 > kbeg || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             bar0 + 8u * sidx)
+                         : "memory");
+        }
+        pending[sidx] = 1;
+    }
+    // drain: every outstanding commit (the MMAs complete in issue order)
+    for (int q = 0; q < 2; ++q) {
+        const int sidx = (it + q) & 1;  // oldest first
+        if (pending[sidx]) {
+            const bool w = __syncthreads_and(mbar_wait(bar0 + 8u * sidx, phase[sidx])) != 0;
+            ok = ok && w;
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else if (kend > kbeg) {
+        // the stages are free now: each warp transposes its 32 rows x 16
+        // columns through 2 KB of them, then writes 64-byte row segments
+        float* tb = reinterpret_cast<float*>(tc_smem) + warp * (32 * 17);
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(ta)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int rr = q * 8 + (lane >> 2), cc = (lane & 3) * 4;
+                const int row = m0 + warp * 32 + rr, col = n0 + c0 + cc;
+                if (row < M && col < N) {
+                    float v[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v[i] = tb[rr * 17 + cc + i];
+                    if (split) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) atomicAdd(z + (size_t)row * ldz + col + i, v[i]);
+                    } else {
+                        if (epi & EPI_BIAS) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) v[i] += bias[col + i];
+                        }
+                        if (z) {
+                            float4* zz = reinterpret_cast<float4*>(z + (size_t)row * ldz + col);
+                            if (epi & EPI_ACC) {
+                                const float4 o = *zz;
+                                *zz = make_float4(o.x + v[0], o.y + v[1], o.z + v[2], o.w + v[3]);
+                            } else {
+                                *zz = make_float4(v[0], v[1], v[2], v[3]);
+                            }
+                        }
+                        if (out) {
+                            if (epi & EPI_SILU) {
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) v[i] = silu(v[i]);
+                            }
+                            const __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
+                            const __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
+                            uint2 pk;
+                            pk.x = *reinterpret_cast<const uint32_t*>(&h0);
+                            pk.y = *reinterpret_cast<const uint32_t*>(&h1);
+                            *reinterpret_cast<uint2*>(out + (size_t)row * ldo + col) = pk;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+constexpr size_t kTcMaxSmem = 2 * (kTcStageA + (size_t)256 * kTcBK * 2);
+
+// C[M][N] = A[M][K] . B[N][K]^T; M % 16 == 0, 16 <= N <= 256 with N % 16 == 0,
+// K % 16 == 0.  Tiles of 128 rows x BN columns; narrower column tiles and a
+// split of K (partial sums added atomically into z) when there are too few
+// tiles to occupy the GPU.
+void gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, const float* bias, int epi, float* z,
+          int ldz, __nv_bfloat16* out, int ldo, int* err, cudaStream_t st)
+{
+    const int mt = (M + kTcBM - 1) / kTcBM;
+    int BN = N;
+    while (BN > 32 && (int64_t)mt * (N / BN) < 128 && (BN / 2) % 16 == 0 && N % (BN / 2) == 0) BN /= 2;
+    int splits = 1;
+    const bool can_split = out == nullptr && epi == 0 && z != nullptr;
+    if (can_split) {
+        while ((int64_t)mt * (N / BN) * splits < 128 && K / (splits * 2) >= 2 * kTcBK) splits *= 2;
+    }
+    const int kpc = splits > 1 ? ((K / splits + kTcBK - 1) / kTcBK) * kTcBK : K;
+    if (splits > 1) cudaMemsetAsync(z, 0, sizeof(float) * (size_t)M * ldz, st);
+    const size_t smem = 2 * (kTcStageA + (size_t)BN * kTcBK * 2);
+    dim3 grid((unsigned)mt, (unsigned)(N / BN), (unsigned)((K + kpc - 1) / kpc));
+    k_gemm_tc<<<grid, 128, smem, st>>>(A, B, M, N, K, BN, kpc, bias, epi, z, ldz, out, ldo, err);
 }
 
 // ---------------------------------------------------------- elementwise
@@ -323,8 +487,9 @@ emc_status ensure_batch(emc_mlp* m, int64_t n)
     return EMC_OK;
 }
 
-// forward on the n rows in m->X; pre-activations and layer inputs kept
-void forward(emc_mlp* m, int64_t n)
+// forward on the n rows in m->X; layer inputs kept, pre-activations kept
+// for every layer when keep_z (training) and for the last layer always
+void forward(emc_mlp* m, int64_t n, bool keep_z = true)
 {
     const int64_t rows = (n + 15) / 16 * 16;
     k_input<<<gridn(rows * m->L[0].in_p, 256), 256, 0, m->st>>>(m->X, n, m->cfg.n_in, m->L[0].in_p, m->norm, m->act[0],
@@ -332,8 +497,8 @@ void forward(emc_mlp* m, int64_t n)
     for (int l = 0; l < m->n_layers; ++l) {
         const Layer& y = m->L[l];
         const bool last = l == m->n_layers - 1;
-        gemm(m->act[l], y.Wb, (int)rows, y.out_p, y.in_p, y.b, EPI_BIAS | (last ? 0 : EPI_SILU), m->z[l], y.out_p,
-             m->act[l + 1], y.out_p, m->st);
+        gemm(m->act[l], y.Wb, (int)rows, y.out_p, y.in_p, y.b, EPI_BIAS | (last ? 0 : EPI_SILU),
+             (keep_z || last) ? m->z[l] : nullptr, y.out_p, m->act[l + 1], y.out_p, m->d_err, m->st);
     }
 }
 
@@ -351,12 +516,12 @@ void backward(emc_mlp* m, int64_t n)
         // dW = dz^T a  (A operand dz^T [out_p][rows], B operand a^T [in_p][rows])
         k_transpose_f2b<<<gridn(nz, 256), 256, 0, m->st>>>(m->dzf, (int)rows, y.out_p, m->dzT);
         k_transpose_b2b<<<gridn(rows * y.in_p, 256), 256, 0, m->st>>>(m->act[l], (int)rows, y.in_p, m->aT);
-        gemm(m->dzT, m->aT, y.out_p, y.in_p, (int)rows, nullptr, 0, y.gW, y.in_p, nullptr, 0, m->st);
+        gemm(m->dzT, m->aT, y.out_p, y.in_p, (int)rows, nullptr, 0, y.gW, y.in_p, nullptr, 0, m->d_err, m->st);
         k_colsum<<<y.out_p, 256, 0, m->st>>>(m->dzf, rows, y.out_p, y.gb);
         if (l == 0) break;
         // da = dz W  (A operand dz [rows][out_p], B operand W^T [in_p][out_p])
         k_f2b<<<gridn(nz, 256), 256, 0, m->st>>>(m->dzf, nz, m->dzb);
-        gemm(m->dzb, y.WTb, (int)rows, y.in_p, y.out_p, nullptr, 0, m->da, y.in_p, nullptr, 0, m->st);
+        gemm(m->dzb, y.WTb, (int)rows, y.in_p, y.out_p, nullptr, 0, m->da, y.in_p, nullptr, 0, m->d_err, m->st);
         const Layer& p = m->L[l - 1];
         k_dsilu<<<gridn(rows * p.out_p, 256), 256, 0, m->st>>>(m->da, m->z[l - 1], rows * p.out_p, p.out_p, p.out,
                                                                m->dzf);
@@ -393,6 +558,19 @@ emc_status pack(emc_mlp* m, std::vector<float>& vec, int dir, bool grads)
             MCK(cudaMemcpyAsync(db, b.data(), 4 * b.size(), cudaMemcpyHostToDevice, m->st));
             MCK(cudaStreamSynchronize(m->st));
         }
+    }
+    return EMC_OK;
+}
+
+// the tensor-core kernels set the error word when a wait expired
+emc_status check_device(emc_mlp* m)
+{
+    int e = 0;
+    MCK(cudaMemcpyAsync(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    MCK(cudaStreamSynchronize(m->st));
+    if (e) {
+        MCK(cudaMemsetAsync(m->d_err, 0, sizeof(int), m->st));
+        return mfail(m, EMC_ETIMEOUT, "tensor-core GEMM: wait for the MMAs expired");
     }
     return EMC_OK;
 }
@@ -454,6 +632,8 @@ emc_status emc_mlp_create(const emc_mlp_config* cfg, void* stream, emc_mlp** out
     std::memcpy(nh + 48, c.y_scale, 64);
     MCK(cudaMemcpyAsync(m->norm, nh, sizeof nh, cudaMemcpyHostToDevice, m->st));
     MCK(malloc0(m, &m->loss, 1));
+    MCK(malloc0(m, &m->d_err, 1));
+    MCK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcMaxSmem));
     emc_status s = refresh_bf16(m);
     if (s != EMC_OK) return s;
     MCK(cudaStreamSynchronize(m->st));
@@ -470,7 +650,7 @@ emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n)
         emc_status s = ensure_batch(m, nn);
         if (s != EMC_OK) return s;
         MCK(cudaMemcpyAsync(m->X, X + r0 * m->cfg.n_in, 4 * nn * m->cfg.n_in, cudaMemcpyHostToDevice, m->st));
-        forward(m, nn);
+        forward(m, nn, false);
         const int last = m->n_layers - 1;
         k_output<<<gridn(nn * m->cfg.n_out, 256), 256, 0, m->st>>>(m->z[last], m->L[last].out_p, nn, m->cfg.n_out,
                                                                    m->norm, m->Y);
@@ -478,7 +658,7 @@ emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n)
         MCK(cudaMemcpyAsync(Y + r0 * m->cfg.n_out, m->Y, 4 * nn * m->cfg.n_out, cudaMemcpyDeviceToHost, m->st));
     }
     MCK(cudaStreamSynchronize(m->st));
-    return EMC_OK;
+    return check_device(m);
 }
 
 emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, float* grad, float* loss)
@@ -493,6 +673,8 @@ emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, f
     MCK(cudaGetLastError());
     if (loss) MCK(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToHost, m->st));
     MCK(cudaStreamSynchronize(m->st));
+    s = check_device(m);
+    if (s != EMC_OK) return s;
     if (grad) {
         std::vector<float> v(n_params(m));
         s = pack(m, v, 0, true);
@@ -544,7 +726,7 @@ emc_status emc_mlp_train(emc_mlp* m, const float* X, const float* Y, int64_t n, 
         MCK(cudaFreeAsync(d_hist, m->st));
     }
     MCK(cudaStreamSynchronize(m->st));
-    return EMC_OK;
+    return check_device(m);
 }
 
 emc_status emc_mlp_params(emc_mlp* m, float* dst, const float* src, int64_t* count)

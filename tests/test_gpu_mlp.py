@@ -61,3 +61,32 @@ def test_params_round_trip(emc):
     X = rng.normal(size=(64, 4)).astype(np.float32)
     want = ref.predict(q.astype(np.float64), sizes, X, nrm)
     assert np.abs(net.infer(X) - want).max() < 3e-2 * np.abs(want - nrm["y_shift"]).max()
+
+
+@pytest.mark.parametrize("hidden", [48, 256])
+def test_ragged_gradient_and_widths(emc, hidden):
+    """1000 rows (the last 128-row tile and the last 64-wide K block of the
+    weight-gradient product are partial) at hidden widths 48 and 256 (tensor
+    memory of 64 and 256 columns)."""
+    net, nrm, sizes, rng = make(emc, hidden=hidden, layers=2, seed=11)
+    X = rng.normal(size=(1000, 4)).astype(np.float32)
+    Y = rng.normal(size=(1000, 7)).astype(np.float32)
+    loss, g = net.grad(X, Y)
+    lref, gref = ref.loss_and_grad(net.params().astype(np.float64), sizes, X, Y, nrm)
+    assert loss == pytest.approx(lref, rel=2e-2)
+    cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    assert cos > 0.999, cos
+    got = net.infer(X)
+    want = ref.predict(net.params().astype(np.float64), sizes, X, nrm)
+    assert np.abs(got - want).max() / np.abs(want - nrm["y_shift"]).max() < 3e-2
+
+
+def test_full_size_inference_sampled(emc):
+    """115,200 queries (1800 subcells x 64 bias points) in one call; sampled
+    rows against the FP64 reference."""
+    net, nrm, sizes, rng = make(emc, seed=13)
+    X = rng.normal(size=(115_200, 4)).astype(np.float32)
+    got = net.infer(X)
+    idx = rng.choice(X.shape[0], 3000, replace=False)
+    want = ref.predict(net.params().astype(np.float64), sizes, X[idx], nrm)
+    assert np.abs(got[idx] - want).max() / np.abs(want - nrm["y_shift"]).max() < 3e-2

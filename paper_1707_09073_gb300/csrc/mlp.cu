@@ -152,16 +152,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 }
 
 // stage the K block [k0, k0 + kb) of rows [r0, r0 + rows) of X (row length
-// K) in the core-matrix layout; rows at or beyond rmax are zero
+// K) in the core-matrix layout with 16-byte asynchronous copies (all in
+// flight at once; the caller commits and waits); rows at or beyond rmax are
+// zero-filled by the copy itself (source size 0)
 __device__ __forceinline__ void tc_stage(unsigned char* dst, const __nv_bfloat16* __restrict__ X, int r0, int rows,
                                          int rmax, int K, int k0, int kb)
 {
     const int nch = kb >> 3;
     for (int i = threadIdx.x; i < rows * nch; i += blockDim.x) {
         const int r = i / nch, c = i - (i / nch) * nch;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (r0 + r < rmax) v = *reinterpret_cast<const uint4*>(X + (size_t)(r0 + r) * K + k0 + 8 * c);
-        *reinterpret_cast<uint4*>(dst + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+        const bool in = r0 + r < rmax;
+        const __nv_bfloat16* src = X + (size_t)(in ? r0 + r : 0) * K + k0 + 8 * c;
+        const uint32_t d = smem_u32(dst + (r >> 3) * 1024 + c * 128 + (r & 7) * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
     }
 }
 
@@ -200,22 +204,43 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
     int pending[2] = {0, 0};  // commits of a stage not yet waited for
     bool ok = true;
     int it = 0;
-    for (int k0 = kbeg; k0 < kend && ok; k0 += kTcBK, ++it) {
+    const int nblk = (kend - kbeg + kTcBK - 1) / kTcBK;
+    // block 0 in flight before the loop; block i + 1 is copied while the
+    // tensor core works on block i
+    if (nblk > 0) {
+        const int kb = min(kTcBK, kend - kbeg);
+        tc_stage(tc_smem, A, m0, kTcBM, M, K, kbeg, kb);
+        tc_stage(tc_smem + kTcStageA, B, n0, BN, N, K, kbeg, kb);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (; it < nblk && ok; ++it) {
         const int sidx = it & 1;
+        const int k0 = kbeg + it * kTcBK;
+        const int kb = min(kTcBK, kend - k0);
+        if (it + 1 < nblk) {
+            const int nx = sidx ^ 1;
+            if (pending[nx]) {
+                // the MMAs that read the next stage (block it - 1) must be
+                // done before it is refilled (on expiry the commit stays
+                // pending and the drain below waits again)
+                ok = __syncthreads_and(mbar_wait(bar0 + 8u * nx, phase[nx])) != 0;
+                if (!ok) break;
+                phase[nx] ^= 1u;
+                pending[nx] = 0;
+            }
+            const int k1 = k0 + kTcBK;
+            const int kb1 = min(kTcBK, kend - k1);
+            unsigned char* nA = tc_smem + nx * stage;
+            tc_stage(nA, A, m0, kTcBM, M, K, k1, kb1);
+            tc_stage(nA + kTcStageA, B, n0, BN, N, K, k1, kb1);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
         unsigned char* sA = tc_smem + sidx * stage;
         unsigned char* sB = sA + kTcStageA;
-        if (pending[sidx]) {
-            // the MMAs that read this stage two blocks ago must be done (on
-            // expiry the commit stays pending and the drain below waits again)
-            ok = __syncthreads_and(mbar_wait(bar0 + 8u * sidx, phase[sidx])) != 0;
-            if (!ok) break;
-            phase[sidx] ^= 1u;
-            pending[sidx] = 0;
-        }
-        const int kb = min(kTcBK, kend - k0);
-        tc_stage(sA, A, m0, kTcBM, M, K, k0, kb);
-        tc_stage(sB, B, n0, BN, N, K, k0, kb);
-        // generic-proxy stores must be visible to the tensor core's reads
+        // the copies must be visible to the tensor core's (async proxy) reads
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -223,7 +248,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
             for (int s = 0; s < (kb >> 4); ++s) {
                 const uint64_t da = tc_sdesc(smem_u32(sA) + 256u * s, 128u, 1024u);
                 const uint64_t db = tc_sdesc(smem_u32(sB) + 256u * s, 128u, 1024u);
-                const uint32_t acc = (k0 > kbeg || s > 0) ? 1u : 0u;
+                const uint32_t acc = (it > 0 || s > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -236,6 +261,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
         }
         pending[sidx] = 1;
     }
+    // no copy may still be landing in shared memory when the CTA moves on
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     // drain: every outstanding commit (the MMAs complete in issue order)
     for (int q = 0; q < 2; ++q) {
         const int sidx = (it + q) & 1;  // oldest first

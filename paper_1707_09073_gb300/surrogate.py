@@ -1,7 +1,8 @@
 """The learned surrogate: local conditions -> Monte Carlo observables.
 
 Inputs per sample: |E| (V/m), field angle to the c axis (rad), lattice
-temperature T (K), log10 of the donor density N_d (m^-3).  Outputs: drift
+temperature T (K), log10 of the donor density N_d (m^-3); the network sees
+the field as ln(1 + |E| / 1 kV/cm).  Outputs: drift
 velocity along -E (m/s), mean kinetic energy (eV), Gamma1/U/Gamma3 fractions,
 net phonon-emission heat per electron (W), current density q N_d v_d
 (A/m^2).  Training data come from batched bulk runs of this library's own
@@ -26,12 +27,26 @@ OUT_NAMES = ("v_drift_m_s", "E_mean_eV", "f_Gamma1", "f_U", "f_Gamma3", "heat_W_
 # sampling box of the inputs: fields up to 2500 kV/cm, the range the drain
 # end of the biased nanowire reaches (its mean field is at most 200 kV/cm)
 BOX = {"E_max": 2.5e8, "T": (300.0, 600.0), "log10_Nd": (22.0, 25.0)}
+# the network sees the field as xi = ln(1 + |E| / E_REF): low fields, where
+# the mobility and its temperature dependence matter, get as much of the
+# input range (and of the training samples) as the saturated high fields
+E_REF = 1.0e5
+XI_MAX = math.log1p(BOX["E_max"] / E_REF)
+
+
+def features(X: np.ndarray) -> np.ndarray:
+    """Network inputs from the physical ones (|E| -> xi, others as they are)."""
+    F = np.array(X, dtype=np.float64, copy=True)
+    F[:, 0] = np.log1p(np.maximum(F[:, 0], 0.0) / E_REF)
+    return F
 
 
 def sample_inputs(n: int, seed: int = 0) -> np.ndarray:
+    """Physical inputs, uniform in xi (so log-like in |E|), angle, T and
+    log10 N_d."""
     rng = np.random.default_rng(seed)
     return np.stack([
-        rng.uniform(0.0, BOX["E_max"], n),
+        E_REF * np.expm1(rng.uniform(0.0, XI_MAX, n)),
         rng.uniform(0.0, math.pi, n),
         rng.uniform(*BOX["T"], n),
         rng.uniform(*BOX["log10_Nd"], n),
@@ -80,8 +95,8 @@ class Surrogate:
 
     def __init__(self, X: np.ndarray, Y: np.ndarray, hidden: int = 128, layers: int = 3, seed: int = 0,
                  stream=None):
-        x_shift = np.array([BOX["E_max"] / 2, math.pi / 2, sum(BOX["T"]) / 2, sum(BOX["log10_Nd"]) / 2])
-        x_scale = np.array([BOX["E_max"] / 2, math.pi / 2, (BOX["T"][1] - BOX["T"][0]) / 2,
+        x_shift = np.array([XI_MAX / 2, math.pi / 2, sum(BOX["T"]) / 2, sum(BOX["log10_Nd"]) / 2])
+        x_scale = np.array([XI_MAX / 2, math.pi / 2, (BOX["T"][1] - BOX["T"][0]) / 2,
                             (BOX["log10_Nd"][1] - BOX["log10_Nd"][0]) / 2])
         y_shift = Y.mean(axis=0)
         y_scale = np.maximum(Y.std(axis=0), 1e-12 * np.maximum(np.abs(y_shift), 1.0))
@@ -90,7 +105,7 @@ class Surrogate:
 
     def fit(self, X: np.ndarray, Y: np.ndarray, steps: int = 4000, batch: int = 1024, lr: float = 1e-3,
             seed: int = 0) -> np.ndarray:
-        return self.net.train(X, Y, steps=steps, batch=batch, lr=lr, seed=seed)
+        return self.net.train(features(X).astype(np.float32), Y, steps=steps, batch=batch, lr=lr, seed=seed)
 
     def predict(self, X: np.ndarray) -> np.ndarray:
-        return self.net.infer(np.asarray(X, dtype=np.float32)).astype(np.float64)
+        return self.net.infer(features(np.asarray(X)).astype(np.float32)).astype(np.float64)

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/emc.h"
@@ -35,6 +36,11 @@ namespace {
 // warm-started from the previous potential, so three sweeps reach the FP64
 // residual floor; a cold start (standalone solve) takes five.
 constexpr int kPoissonSweeps = 3;
+// FP32 production steps: the potential is warm-started from the previous
+// Poisson period, and one FP64-refined sweep with the FP32 inverse leaves a
+// relative error of ~1e-7 (the precision of the FP32 field) even after a
+// 10% change; the parity build, the first solve and bias changes keep three
+constexpr int kPoissonSweepsStepF32 = 1;
 constexpr int kSmemTableKiB = 32;  // default rate-table bytes staged per block
 constexpr int kMaxCells = 8192;                 // dense FP64 Poisson inverse limit
 
@@ -683,7 +689,7 @@ emc_status poisson_setup(emc_ctx* ctx)
 
 // rhs from the subcell counts -> kPoissonSweeps refinement sweeps -> field
 template <typename Real>
-emc_status poisson_update(emc_ctx* ctx)
+emc_status poisson_update(emc_ctx* ctx, int sweeps = kPoissonSweeps)
 {
     const int n = ctx->ncell, E = ctx->n_ens;
     const int64_t tot = (int64_t)E * n;
@@ -691,13 +697,13 @@ emc_status poisson_update(emc_ctx* ctx)
     const double Vcell = ctx->dx * ctx->dy * ctx->dz;
     k_rhs<<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->charge, nullptr, ctx->d_w, ctx->d_Nd, Vcell,
                                                    kE2Eps0 / ctx->cfg[0].eps_s, ctx->d_bias, ctx->rhs);
-    for (int s = 0; s < kPoissonSweeps; ++s) {
+    for (int s = 0; s < sweeps; ++s) {
         k_resid<<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->rhs, ctx->phi, ctx->r32);
         launch_sweep(ctx->G32, ctx->r32, ctx->part, ctx->phi, n, E, ctx->st);
     }
     k_field<Real><<<grid_for(tot, 256), 256, 0, ctx->st>>>(G, E, ctx->phi, ctx->dx, ctx->dy, ctx->dz, ctx->Efield,
                                                            static_cast<Real*>(ctx->acc_cell));
-    ctx->launches += 2 + 3 * kPoissonSweeps;
+    ctx->launches += 2 + 3 * sweeps;
     CK(cudaGetLastError());
     return EMC_OK;
 }
@@ -994,17 +1000,18 @@ emc_status init_impl(emc_ctx* ctx)
 template <typename Real>
 emc_status chunk_tail(emc_ctx* ctx)
 {
+    const int sweeps = std::is_same<Real, float>::value ? kPoissonSweepsStepF32 : kPoissonSweeps;
     if (!ctx->use_graph) {
         launch_inject<Real>(ctx->P, ctx->st);
         ctx->launches += 1;
-        return poisson_update<Real>(ctx);
+        return poisson_update<Real>(ctx, sweeps);
     }
     if (!ctx->g_tail_exec) {
         const int64_t l0 = ctx->launches;
         CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
         launch_inject<Real>(ctx->P, ctx->st);
         ctx->launches += 1;
-        emc_status s = poisson_update<Real>(ctx);
+        emc_status s = poisson_update<Real>(ctx, sweeps);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
         if (s != EMC_OK) return s;

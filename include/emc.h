@@ -206,12 +206,15 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null,
  * contact subcell's temperature.  The first call builds the 151 bin tables. */
 emc_status emc_set_temperature(emc_ctx* ctx, int32_t ens, const double* T_cells, int32_t n);
 
-/* Set the terminal voltages of ensemble ens and re-solve its field. */
+/* Set the terminal voltages of ensemble ens and re-solve the fields (the
+ * solve is skipped when no voltage changed: the field already belongs to
+ * them). */
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg);
 
 /* Set the terminal voltages of every ensemble from host array bias[E][3]
  * ({Vs, Vd, Vg} per ensemble) and re-solve the fields: one host-to-device
- * copy of 24 E bytes (asynchronous if bias is pinned). */
+ * copy of 24 E bytes (asynchronous if bias is pinned); the solve is skipped
+ * when no voltage changed. */
 emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias);
 
 /* Kernel timing: with enable = 1 every later flight-kernel launch is

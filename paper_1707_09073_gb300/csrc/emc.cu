@@ -1470,12 +1470,16 @@ emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double 
 {
     if (!ctx || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias needs the nanowire geometry");
+    const bool same = ctx->bias[3 * ens] == Vs && ctx->bias[3 * ens + 1] == Vd && ctx->bias[3 * ens + 2] == Vg;
     ctx->bias[3 * ens] = Vs;
     ctx->bias[3 * ens + 1] = Vd;
     ctx->bias[3 * ens + 2] = Vg;
     CK(cudaMemcpyAsync(ctx->d_bias + 3 * ens, &ctx->bias[3 * ens], 24, cudaMemcpyHostToDevice, ctx->st));
-    emc_status s = ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
-    if (s != EMC_OK) return s;
+    // the field already belongs to these terminal voltages when none changed
+    if (!same) {
+        emc_status s = ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
+        if (s != EMC_OK) return s;
+    }
     CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
 }
@@ -1484,8 +1488,11 @@ emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias)
 {
     if (!ctx || !bias) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias_all needs the nanowire geometry");
+    const bool same = std::memcmp(ctx->bias.data(), bias, sizeof(double) * 3 * ctx->n_ens) == 0;
     std::memcpy(ctx->bias.data(), bias, sizeof(double) * 3 * ctx->n_ens);
     CK(cudaMemcpyAsync(ctx->d_bias, bias, sizeof(double) * 3 * ctx->n_ens, cudaMemcpyHostToDevice, ctx->st));
+    // the field already belongs to these terminal voltages when none changed
+    if (same) return EMC_OK;
     return ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
 }
 

@@ -319,3 +319,22 @@ def test_live_contexts_with_different_shared_memory(emc):
             small.close()
     finally:
         big.close()
+
+
+def test_set_bias_resolves_only_on_change(emc):
+    """Unchanged terminal voltages leave the field as it is (no solve is
+    launched); a changed drain voltage re-solves it."""
+    cfgs = [W.nanowire(n_particles=2000, nx=10, Lx=100e-9, Vd=float(v), seed=60 + v) for v in (1, 3)]
+    bias = np.array([[c["Vs"], c["Vd"], c["Vg"]] for c in cfgs])
+    with emc.Context(cfgs) as ctx:
+        ctx.emc_step(10)
+        phi0 = ctx.emc_tally(emc.TALLY_PHI).copy()
+        n0 = ctx.launch_count()
+        ctx.emc_set_bias_all(bias.ctypes.data)
+        assert ctx.launch_count() == n0
+        assert np.array_equal(ctx.emc_tally(emc.TALLY_PHI), phi0)
+        bias[1, 1] = 5.0
+        ctx.emc_set_bias_all(bias.ctypes.data)
+        assert ctx.launch_count() > n0
+        phi1 = ctx.emc_tally(emc.TALLY_PHI)
+        assert phi1[1, -1] > phi0[1, -1] + 1.0

@@ -417,8 +417,9 @@ def run_emc(args, world: int, rank: int, local: int):
     bias = torch.zeros((E, 3), dtype=torch.float64).pin_memory()
     for e, c in enumerate(cfgs):
         bias[e, 0], bias[e, 1], bias[e, 2] = c["Vs"], c["Vd"], c["Vg"]
-    heat = np.zeros((E, ctx.n_cell, 2), dtype=np.int64)
-    cross = np.zeros((E, 4), dtype=np.int64)
+    # results land in pinned host memory, like the bias that goes in
+    heat = torch.zeros((E, ctx.n_cell, 2), dtype=torch.int64).pin_memory().numpy()
+    cross = torch.zeros((E, 4), dtype=torch.int64).pin_memory().numpy()
     n_e2e = max(1, min(args.steps, args.e2e_steps))
     with torch.cuda.stream(stream):
         ctx.emc_tally(emc.TALLY_OBS, reset=True)
@@ -490,7 +491,7 @@ def run_emc(args, world: int, rank: int, local: int):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": ev2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": n_e2e, "path": "emc_set_bias_all (pinned host) + emc_step + emc_tally OBS/HEAT/CROSSINGS to host"},
+                "steps": n_e2e, "path": "emc_set_bias_all (pinned host) + emc_step + emc_tally OBS/HEAT/CROSSINGS to host (heat map and crossings into pinned host buffers)"},
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
                    "samples": clocks["samples"]},
         "gpu_launches": launches,

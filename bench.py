@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -387,8 +388,9 @@ def run_emc(args, world: int, rank: int, local: int):
             ctx.emc_step(steps)
         ctx.emc_tally(emc.TALLY_OBS, reset=True)
         launches0 = ctx.launch_count()
-        sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+        # raw clock samples go to $EMC_ARTIFACT_DIR when set (the summary is in the JSON line)
+        art = os.environ.get("EMC_ARTIFACT_DIR") or tempfile.gettempdir()
+        sampler = ClockSampler(local, os.path.join(art, f"clocks_rank{rank}.csv"))
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
@@ -521,7 +523,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
-    ap.add_argument("--sur-samples", type=int, default=8192)
+    ap.add_argument("--sur-samples", type=int, default=100_000)
     ap.add_argument("--h-bottom", type=float, default=5e8)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -338,3 +338,37 @@ def test_set_bias_resolves_only_on_change(emc):
         assert ctx.launch_count() > n0
         phi1 = ctx.emc_tally(emc.TALLY_PHI)
         assert phi1[1, -1] > phi0[1, -1] + 1.0
+
+
+def test_small_bulk_workload_in_full(emc, oracle_mod):
+    """The small bulk workload as specified (10,000 electrons, 100 kV/cm,
+    1e17 cm^-3, 300 K, Philox seed 0, 2 ps = 2000 steps), parity build
+    against the oracle.  Every particle takes the same discrete path: the
+    same number of random draws (Philox counter) and the same final valley,
+    and every event count is equal.  The continuous state does not stay
+    bit-equal over 2e7 particle-steps: scattering angles are drawn relative to
+    the incoming direction, so the two sides' different floating-point
+    operation orders (1e-14 relative after 200 steps) grow chaotically
+    (median 1.6e-9, largest ~7% after 2000 steps); drift velocity, mean
+    energy and valley occupancy agree to 1e-6."""
+    cfg = W.config_bulk_small()
+    steps = W.BULK_SMALL_STEPS
+    n = cfg["n_particles"]
+    ref = oracle_mod.Sim(cfg)
+    ref.run(steps)
+    rt = ref.tallies()
+    o = ref.particles()
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        g = gpu_tallies(emc, ctx)
+        p = ctx.debug_particles()
+    assert np.array_equal(p["ctr"][:n], o["ctr"][:n])
+    assert np.array_equal(p["valley"][:n], o["valley"][:n])
+    assert np.array_equal(g["events"], rt["events"].sum(axis=0))
+    ob = g["obs"]
+    assert np.array_equal(ob["self_events"], rt["self_events"].astype(np.int64))
+    assert np.array_equal(ob["valley_steps"], rt["valley_steps"])
+    assert ob["n_samples"] == rt["n_samples"] == n * steps
+    assert ob["sum_v"][2] == pytest.approx(rt["sum_v"][2], rel=1e-6)
+    np.testing.assert_allclose(ob["sum_v"][:2], rt["sum_v"][:2], atol=1e-6 * abs(rt["sum_v"][2]))
+    assert ob["sum_E"] == pytest.approx(rt["sum_E"], rel=1e-6)

@@ -824,17 +824,18 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
     int* scan = shi + ncon + 1;
     uint32_t* ids = reinterpret_cast<uint32_t*>(scan + blockDim.x);
     __shared__ int n_src, n_drn;
+    // deficits of the contact cells, loaded in parallel, then their prefix
+    // sums (pre[t] = electrons missing in contacts 0 .. t-1)
+    for (int t = threadIdx.x; t < ncon; t += blockDim.x) {
+        const int side = t / nface, rem = t - side * nface;
+        const int ix = side ? P.nx - 1 : 0;
+        const int need = P.n_target[e] - P.charge[(size_t)e * P.ncell + ix * nface + rem];
+        pre[t + 1] = need > 0 ? need : 0;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        int acc = 0;
         pre[0] = 0;
-        for (int t = 0; t < ncon; ++t) {
-            const int side = t / nface, rem = t - side * nface;
-            const int ix = side ? P.nx - 1 : 0;
-            const int cell = ix * nface + rem;
-            const int need = P.n_target[e] - P.charge[(size_t)e * P.ncell + cell];
-            acc += need > 0 ? need : 0;
-            pre[t + 1] = acc;
-        }
+        for (int t = 0; t < ncon; ++t) pre[t + 1] += pre[t];
         n_src = 0;
         n_drn = 0;
     }

@@ -419,23 +419,32 @@ def run_emc(args, world: int, rank: int, local: int):
     bias = torch.zeros((E, 3), dtype=torch.float64).pin_memory()
     for e, c in enumerate(cfgs):
         bias[e, 0], bias[e, 1], bias[e, 2] = c["Vs"], c["Vd"], c["Vg"]
-    # results land in pinned host memory, like the bias that goes in
-    heat = torch.zeros((E, ctx.n_cell, 2), dtype=torch.int64).pin_memory().numpy()
-    cross = torch.zeros((E, 4), dtype=torch.int64).pin_memory().numpy()
+    # results land in page-locked host memory, like the bias that goes in;
+    # two buffer sets, so step i + 1 is enqueued before step i's results are
+    # waited for (every step's results still reach the host inside the timed
+    # region)
+    bufs = [(ctx.pinned_tally(emc.TALLY_OBS), ctx.pinned_tally(emc.TALLY_HEAT), ctx.pinned_tally(emc.TALLY_CROSSINGS))
+            for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
     n_e2e = max(1, min(args.steps, args.e2e_steps))
     with torch.cuda.stream(stream):
         ctx.emc_tally(emc.TALLY_OBS, reset=True)
         torch.cuda.synchronize(dev)
         w0 = time.perf_counter()
-        for _ in range(n_e2e):
+        for i in range(n_e2e):
             ctx.emc_set_bias_all(bias.data_ptr())
             ctx.emc_step(steps)
-            ctx.emc_tally(emc.TALLY_OBS)
-            ctx.emc_tally(emc.TALLY_HEAT, out=heat)
-            ctx.emc_tally(emc.TALLY_CROSSINGS, out=cross)
-        torch.cuda.synchronize(dev)
+            ob, ht, cr = bufs[i % 2]
+            ctx.emc_tally_async(emc.TALLY_OBS, ob)
+            ctx.emc_tally_async(emc.TALLY_HEAT, ht)
+            ctx.emc_tally_async(emc.TALLY_CROSSINGS, cr)
+            done[i % 2].record(stream)
+            if i > 0:
+                done[(i - 1) % 2].synchronize()
+        done[(n_e2e - 1) % 2].synchronize()
         e2e_s = time.perf_counter() - w0
         ev2 = int(ctx.emc_tally(emc.TALLY_EVENTS, reset=True).sum())
+    heat, cross = bufs[0][1], bufs[0][2]
     h2d = E * 3 * 8
     d2h = E * 128 + heat.nbytes + cross.nbytes
 
@@ -493,7 +502,7 @@ def run_emc(args, world: int, rank: int, local: int):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": ev2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": n_e2e, "path": "emc_set_bias_all (pinned host) + emc_step + emc_tally OBS/HEAT/CROSSINGS to host (heat map and crossings into pinned host buffers)"},
+                "steps": n_e2e, "path": "emc_set_bias_all (pinned host) + emc_step + emc_tally_async OBS/HEAT/CROSSINGS into pinned host buffers, double-buffered: step i+1 enqueued before step i's results are waited for"},
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
                    "samples": clocks["samples"]},
         "gpu_launches": launches,

@@ -162,6 +162,20 @@ emc_status emc_step(emc_ctx* ctx, int32_t n_steps);
 emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes,
                      int32_t dst_is_device, int32_t reset);
 
+/* The same tally and reset as emc_tally, enqueued on the context stream
+ * without waiting for it: the values are packed on the device (the same
+ * conversions) and copied to dst in stream order, after the work enqueued
+ * before this call.  For the copy to be asynchronous a host dst must be
+ * page-locked (pageable memory makes it synchronous).  dst must stay valid,
+ * and must not be read, until the stream has passed the copy: synchronise
+ * the stream, or wait on an event recorded on it after this call.  This lets
+ * a caller enqueue the next emc_step before reading the previous step's
+ * tallies.  The first call allocates a small staging buffer (the largest
+ * tally's size).  Device errors of the steps are reported by the next
+ * emc_tally, not here. */
+emc_status emc_tally_async(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes,
+                           int32_t dst_is_device, int32_t reset);
+
 /* FP64 Poisson solve on the context's subcell grid (nanowire only), for
  * ensemble 0 of the context:  div(eps_s eps0 grad phi) = -rho with the
  * Dirichlet terminal faces at bc_volts = {Vs, Vd, Vg}.  charge_or_null: host

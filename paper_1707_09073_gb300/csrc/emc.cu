@@ -101,6 +101,10 @@ struct emc_ctx {
     // Poisson
     double *Lmat = nullptr, *Ginv = nullptr, *phi = nullptr, *rhs = nullptr, *Efield = nullptr, *d_bias = nullptr,
            *d_w = nullptr, *d_Nd = nullptr;
+    // emc_tally_async: packed-tally staging buffer and per-ensemble
+    // parameters {hw_lo, hw_iv, w, Fx, Fy, Fz}, allocated on first use
+    unsigned char* tstage = nullptr;
+    double* tpar = nullptr;
     float *G32 = nullptr, *r32 = nullptr, *part = nullptr;
     uint8_t* d_gate = nullptr;
     std::vector<void*> allocs;
@@ -952,6 +956,74 @@ emc_status set_temperature_impl(emc_ctx* ctx, int ens, const double* T, int n)
     return EMC_OK;
 }
 
+// bytes of tally `kind` for E ensembles of C subcells (0: unknown kind)
+size_t tally_bytes(int E, int C, int kind)
+{
+    switch (kind) {
+    case EMC_TALLY_OBS: return sizeof(emc_obs) * (size_t)E;
+    case EMC_TALLY_EVENTS: return 8ull * E * NV * NM;
+    case EMC_TALLY_HEAT: return 8ull * E * C * 2;
+    case EMC_TALLY_CHARGE: return 8ull * E * C;
+    case EMC_TALLY_CROSSINGS: return 8ull * E * 4;
+    case EMC_TALLY_PHI: return 8ull * E * C;
+    case EMC_TALLY_FIELD: return 8ull * E * C * 3;
+    case EMC_TALLY_HEAT_J: return 8ull * E * C;
+    default: return 0;
+    }
+}
+
+// A tally in its ABI layout, computed on the device from the accumulators
+// (the same conversions emc_tally does on the host): observations and
+// crossings per ensemble, subcell charge (bulk: live count), heat in joules
+// (net phonons x energy x superparticle weight), and the zero potential and
+// uniform field of bulk ensembles.  par[E][6] = {hw_lo, hw_iv, w, Fx, Fy, Fz}.
+__global__ void k_tally_pack(int kind, int E, int C, int nw, const unsigned long long* cnt, const double* sums,
+                             const long long* alive, const int* charge, const long long* heat, const double* par,
+                             long long steps_done, void* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (kind == EMC_TALLY_OBS) {
+        if (i >= E) return;
+        const unsigned long long* c = cnt + i * NCNT;
+        const double* sm = sums + i * NSUM;
+        emc_obs q;
+        for (int k = 0; k < 3; ++k) q.sum_v[k] = sm[SUM_VX + k] * 1e6;
+        q.sum_E = sm[SUM_E] * kQ;
+        q.sum_Etot = sm[SUM_ETOT] * kQ;
+        q.n_samples = (int64_t)c[CNT_SAMPLES];
+        for (int k = 0; k < 3; ++k) {
+            q.valley_steps[k] = (int64_t)c[CNT_V0 + k];
+            q.self_events[k] = (int64_t)c[CNT_SELF0 + k];
+        }
+        q.overflow = (int64_t)c[CNT_OVERFLOW];
+        q.steps_done = steps_done;
+        q.n_alive = (int64_t)alive[i];
+        q.inject_starved = (int64_t)c[CNT_STARVED];
+        static_cast<emc_obs*>(out)[i] = q;
+    } else if (kind == EMC_TALLY_CROSSINGS) {
+        if (i >= E) return;
+        int64_t* o = static_cast<int64_t*>(out) + 4 * i;
+        const unsigned long long* c = cnt + i * NCNT;
+        o[0] = (int64_t)c[CNT_SRC_OUT];
+        o[1] = (int64_t)c[CNT_DRN_OUT];
+        o[2] = (int64_t)c[CNT_SRC_IN];
+        o[3] = (int64_t)c[CNT_DRN_IN];
+    } else if (kind == EMC_TALLY_CHARGE) {
+        if (i >= (int64_t)E * C) return;
+        static_cast<int64_t*>(out)[i] = nw ? (int64_t)charge[i] : (int64_t)alive[i / C];
+    } else if (kind == EMC_TALLY_HEAT_J) {
+        if (i >= (int64_t)E * C) return;
+        const double* p = par + 6 * (i / C);
+        static_cast<double*>(out)[i] = ((double)heat[2 * i] * p[0] + (double)heat[2 * i + 1] * p[1]) * kQ * p[2];
+    } else if (kind == EMC_TALLY_PHI) {
+        if (i >= (int64_t)E * C) return;
+        static_cast<double*>(out)[i] = 0.0;
+    } else if (kind == EMC_TALLY_FIELD) {
+        if (i >= (int64_t)E * C * 3) return;
+        static_cast<double*>(out)[i] = par[6 * (i / (3 * C)) + 3 + i % 3];
+    }
+}
+
 emc_status check_err(emc_ctx* ctx)
 {
     int h = 0;
@@ -1321,6 +1393,55 @@ emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_
         CK(cudaMemsetAsync(ctx->heat, 0, 8ull * E * C * 2, ctx->st));
     }
     CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status emc_tally_async(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_t dst_is_device, int32_t reset)
+{
+    if (!ctx || !dst) return EMC_EINVAL;
+    const int E = ctx->n_ens, C = ctx->ncell;
+    const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
+    const size_t need = tally_bytes(E, C, kind);
+    if (need == 0) return fail(ctx, EMC_EINVAL, "unknown tally kind");
+    if (bytes < need) return fail(ctx, EMC_EINVAL, "destination too small");
+    const cudaMemcpyKind dir = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const void* direct = kind == EMC_TALLY_EVENTS ? (const void*)ctx->events
+                       : kind == EMC_TALLY_HEAT ? (const void*)ctx->heat
+                       : (nw && kind == EMC_TALLY_PHI) ? (const void*)ctx->phi
+                       : (nw && kind == EMC_TALLY_FIELD) ? (const void*)ctx->Efield : nullptr;
+    if (direct) {
+        CK(cudaMemcpyAsync(dst, direct, need, dir, ctx->st));
+    } else {
+        if (!ctx->tstage) {
+            CK(dalloc(ctx, &ctx->tstage, tally_bytes(E, C, EMC_TALLY_FIELD) + sizeof(emc_obs) * E));
+            CK(dalloc(ctx, &ctx->tpar, (size_t)6 * E));
+            std::vector<double> par((size_t)6 * E);
+            for (int e = 0; e < E; ++e) {
+                const emc_config& c = ctx->cfg[e];
+                double* q = &par[(size_t)6 * e];
+                q[0] = c.hw_lo_eV; q[1] = c.hw_iv_eV; q[2] = ctx->w[e];
+                q[3] = nw ? 0.0 : c.field_V_m[0]; q[4] = nw ? 0.0 : c.field_V_m[1]; q[5] = nw ? 0.0 : c.field_V_m[2];
+            }
+            CK(cudaMemcpyAsync(ctx->tpar, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice, ctx->st));
+            // the parameters must be on the device before the host vector goes
+            CK(cudaStreamSynchronize(ctx->st));
+        }
+        void* out = dst_is_device ? dst : (void*)ctx->tstage;
+        const int64_t items = kind == EMC_TALLY_OBS || kind == EMC_TALLY_CROSSINGS ? E
+                            : kind == EMC_TALLY_FIELD ? (int64_t)E * C * 3 : (int64_t)E * C;
+        k_tally_pack<<<grid_for(items, 256), 256, 0, ctx->st>>>(kind, E, C, nw ? 1 : 0, ctx->cnt, ctx->sums, ctx->alive,
+                                                                  ctx->charge, ctx->heat, ctx->tpar, ctx->steps_done,
+                                                                  out);
+        ctx->launches += 1;
+        if (!dst_is_device) CK(cudaMemcpyAsync(dst, ctx->tstage, need, cudaMemcpyDeviceToHost, ctx->st));
+    }
+    if (reset) {
+        CK(cudaMemsetAsync(ctx->events, 0, 8ull * E * NV * NM, ctx->st));
+        CK(cudaMemsetAsync(ctx->cnt, 0, 8ull * E * NCNT, ctx->st));
+        CK(cudaMemsetAsync(ctx->sums, 0, 8ull * E * NSUM, ctx->st));
+        CK(cudaMemsetAsync(ctx->heat, 0, 8ull * E * C * 2, ctx->st));
+    }
+    CK(cudaGetLastError());
     return EMC_OK;
 }
 

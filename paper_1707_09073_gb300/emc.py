@@ -75,6 +75,7 @@ def lib():
         L.emc_batch_init.argtypes = [C.POINTER(EmcConfig), I32, P, C.POINTER(P)]
         L.emc_step.argtypes = [P, I32]
         L.emc_tally.argtypes = [P, I32, P, C.c_size_t, I32, I32]
+        L.emc_tally_async.argtypes = [P, I32, P, C.c_size_t, I32, I32]
         L.poisson_solve.argtypes = [P, dp, dp, dp]
         L.emc_poisson_solve_static.argtypes = [P, dp, dp, dp]
         L.emc_set_bias.argtypes = [P, I32, C.c_double, C.c_double, C.c_double]
@@ -92,7 +93,7 @@ def lib():
         L.emc_last_error.argtypes = [P]
         L.emc_last_error.restype = C.c_char_p
         L.emc_destroy.argtypes = [P]
-        for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "poisson_solve",
+        for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "emc_tally_async", "poisson_solve",
                   "emc_poisson_solve_static", "emc_set_bias",
                   "emc_set_bias_all", "emc_set_temperature", "emc_profile", "emc_profile_read",
                   "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape"):
@@ -146,6 +147,7 @@ class Context:
         self.cfgs = [dict(c) for c in cfgs]
         arr = (EmcConfig * len(cfgs))(*[make_config(c, precision) for c in cfgs])
         self._arr = arr
+        self._pinned = []  # page-locked buffers handed out by pinned_tally
         self.h = C.c_void_p()
         st = lib().emc_batch_init(arr, len(cfgs), C.c_void_p(stream or 0), C.byref(self.h))
         if st != 0:
@@ -178,6 +180,49 @@ class Context:
     def emc_step(self, n_steps: int):
         self._check(lib().emc_step(self.h, int(n_steps)))
 
+    def _tally_spec(self, kind: int):
+        E, Cc = self.n_ens, self.n_cell
+        return {
+            TALLY_OBS: (OBS_DTYPE, (E,)),
+            TALLY_EVENTS: (np.dtype(np.uint64), (E, NV, NM)),
+            TALLY_HEAT: (np.dtype(np.int64), (E, Cc, 2)),
+            TALLY_CHARGE: (np.dtype(np.int64), (E, Cc)),
+            TALLY_CROSSINGS: (np.dtype(np.int64), (E, 4)),
+            TALLY_PHI: (np.dtype(np.float64), (E, Cc)),
+            TALLY_FIELD: (np.dtype(np.float64), (E, Cc, 3)),
+            TALLY_HEAT_J: (np.dtype(np.float64), (E, Cc)),
+        }[kind]
+
+    def pinned_tally(self, kind: int) -> np.ndarray:
+        """A page-locked host array of tally `kind`'s shape and type (OBS:
+        structured array like obs_buffer) for emc_tally_async."""
+        import torch
+        dt, shape = self._tally_spec(kind)
+        n = int(np.prod(shape)) * dt.itemsize
+        t = torch.empty(n, dtype=torch.uint8).pin_memory()
+        self._pinned.append(t)
+        return t.numpy().view(dt).reshape(shape)
+
+    def emc_tally_async(self, kind: int, out, reset: bool = False, device: bool = False):
+        """Enqueue tally `kind` into ``out`` (page-locked host array from
+        pinned_tally, or with ``device=True`` a device pointer) without
+        waiting; read it after synchronising the stream (or an event recorded
+        after this call)."""
+        dt, shape = self._tally_spec(kind)
+        nbytes = int(np.prod(shape)) * dt.itemsize
+        if device:
+            self._check(lib().emc_tally_async(self.h, kind, C.c_void_p(int(out)), nbytes, 1, int(reset)))
+        else:
+            if out.nbytes < nbytes or out.dtype != dt:
+                raise ValueError("out must be pinned_tally(kind) of this context")
+            self._check(lib().emc_tally_async(self.h, kind, out.ctypes.data_as(C.c_void_p), out.nbytes, 0, int(reset)))
+        return out
+
+    def obs_buffer(self) -> np.ndarray:
+        """A structured array [n_ens] (fields as in emc_obs) for
+        emc_tally(TALLY_OBS, out=...): the fast path for per-step reads."""
+        return np.zeros(self.n_ens, dtype=OBS_DTYPE)
+
     def emc_tally(self, kind: int, reset: bool = False, out=None, device: bool = False):
         """Copy a tally (numpy array on the host, or into ``out`` when given:
         a numpy array, or with ``device=True`` a device pointer (int) of at
@@ -198,6 +243,13 @@ class Context:
             self._check(lib().emc_tally(self.h, kind, C.c_void_p(int(out)), nbytes, 1, int(reset)))
             return out
         if kind == TALLY_OBS:
+            if out is not None:
+                # preallocated structured array (obs_buffer()): filled in place,
+                # no per-ensemble Python objects
+                if out.dtype != OBS_DTYPE or out.size != E:
+                    raise ValueError("out must be obs_buffer() of this context")
+                self._check(lib().emc_tally(self.h, kind, out.ctypes.data_as(C.c_void_p), out.nbytes, 0, int(reset)))
+                return out
             buf = spec[0]()
             self._check(lib().emc_tally(self.h, kind, C.byref(buf), C.sizeof(buf), 0, int(reset)))
             return [obs_dict(buf[e]) for e in range(E)]
@@ -269,6 +321,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().emc_launch_count(self.h))
+
+
+# the observation tally as a numpy structured dtype (same layout as emc_obs)
+OBS_DTYPE = np.dtype(EmcObs)
 
 
 def obs_dict(o: EmcObs) -> dict:

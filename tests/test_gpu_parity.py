@@ -372,3 +372,16 @@ def test_small_bulk_workload_in_full(emc, oracle_mod):
     assert ob["sum_v"][2] == pytest.approx(rt["sum_v"][2], rel=1e-6)
     np.testing.assert_allclose(ob["sum_v"][:2], rt["sum_v"][:2], atol=1e-6 * abs(rt["sum_v"][2]))
     assert ob["sum_E"] == pytest.approx(rt["sum_E"], rel=1e-6)
+
+
+def test_obs_buffer_matches_dicts(emc):
+    """The in-place observation read (structured array) carries the same
+    values as the list-of-dicts read."""
+    cfgs = [W.bulk(n_particles=500 + 100 * e, seed=70 + e) for e in range(3)]
+    with emc.Context(cfgs) as ctx:
+        ctx.emc_step(20)
+        dicts = ctx.emc_tally(emc.TALLY_OBS)
+        buf = ctx.emc_tally(emc.TALLY_OBS, out=ctx.obs_buffer())
+    for e, d in enumerate(dicts):
+        for k, v in d.items():
+            assert np.array_equal(np.asarray(buf[k][e]), np.asarray(v)), (e, k)

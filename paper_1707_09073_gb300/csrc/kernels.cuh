@@ -804,14 +804,12 @@ __global__ void k_init(const DevParams P)
 // --------------------------------------------------------------- inject
 // Refill each contact subcell (the x = 0 layer first, then x = Lx, cells in
 // (y, z) order) up to n_target electrons, taking free ids of the ensemble in
-// increasing order: the r-th free id fills the r-th missing electron.
-// Blocks (e, b): each of the gridDim.y blocks of ensemble e scans the whole
-// free-id bitmap (threads own contiguous words; a block scan of the words'
-// population counts gives each free id its rank) and draws the electrons of
-// its own share of the ranks: ids are gathered by rank into shared memory
-// (INJ per round), the new electrons drawn in parallel, and the block clears
-// the bits it took with atomic ANDs.  Dynamic shared memory: the deficit
-// prefix sums (2 ny nz + 1 ints), a scan buffer (blockDim ints) and INJ ids.
+// increasing order: the r-th free id fills the r-th missing electron.  One
+// block per ensemble.  Threads own contiguous words of the free-id bitmap;
+// a block scan of the words' population counts gives each free id its rank,
+// ids are gathered by rank into shared memory (INJ per round) and the new
+// electrons are drawn in parallel.  Dynamic shared memory: the deficit prefix
+// sums (2 ny nz + 1 ints), a scan buffer (blockDim ints) and INJ ids.
 constexpr int INJ = 1024;
 
 template <typename Real>
@@ -860,15 +858,12 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
     const int total = scan[blockDim.x - 1];
     const int base = scan[threadIdx.x] - mine;
     const int Deff = D < total ? D : total;
-    if (threadIdx.x == 0 && blockIdx.y == 0 && total < D)
+    if (threadIdx.x == 0 && total < D)
         atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_STARVED], (unsigned long long)(D - total));
-    // this block's share of the ranks
-    const int share = (Deff + (int)gridDim.y - 1) / (int)gridDim.y;
-    const int rb0 = min(Deff, (int)blockIdx.y * share), rb1 = min(Deff, rb0 + share);
     const Phys<Real>* ph = static_cast<const Phys<Real>*>(P.phys) + P.tabset[e];
     const Real len3[3] = {Real(P.dx), Real(P.dy), Real(P.dz)};
-    for (int r0 = rb0; r0 < rb1; r0 += INJ) {
-        const int r1 = min(rb1, r0 + INJ);
+    for (int r0 = 0; r0 < Deff; r0 += INJ) {
+        const int r1 = min(Deff, r0 + INJ);
         // gather the ids of ranks [r0, r1) by rank
         int rank = base;
         for (int64_t w = w0; w < w1 && rank < r1; ++w) {
@@ -916,18 +911,20 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
         }
         __syncthreads();
     }
-    // clear the bits of the ids this block took (ranks [rb0, rb1)); other
-    // blocks of the ensemble clear other bits of the same words
+    // clear the bits of the ids taken (ranks below Deff).  The whole
+    // ensemble is one block, so every thread's scan of the bitmap above has
+    // finished before any bit changes (several blocks per ensemble would
+    // rank against a bitmap that others are already clearing)
     int rank = base;
-    for (int64_t w = w0; w < w1 && rank < rb1; ++w) {
+    for (int64_t w = w0; w < w1 && rank < Deff; ++w) {
         uint32_t word = bits[w], clear = 0u;
-        while (word && rank < rb1) {
+        while (word && rank < Deff) {
             const int bit = __ffs(word) - 1;
             word &= word - 1u;
-            if (rank >= rb0) clear |= 1u << bit;
+            clear |= 1u << bit;
             ++rank;
         }
-        if (clear) atomicAnd(&bits[w], ~clear);
+        bits[w] &= ~clear;
     }
     if (threadIdx.x == 0) {
         atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_SRC_IN], (unsigned long long)n_src);
@@ -1121,15 +1118,12 @@ void launch_init(const DevParams& P, bool nw, cudaStream_t st)
         k_init<Real, false><<<grid, 256, 0, st>>>(P);
 }
 
-// blocks per ensemble for the contact refill (each draws a share of the ranks)
-constexpr unsigned kInjectBlocks = 8;
-
 template <typename Real>
 void launch_inject(const DevParams& P, cudaStream_t st)
 {
     const int block = 256;
     const size_t smem = sizeof(int) * (2 * P.ny * P.nz + 1 + block + INJ);
-    k_inject<Real><<<dim3((unsigned)P.n_ens, kInjectBlocks), block, smem, st>>>(P);
+    k_inject<Real><<<P.n_ens, block, smem, st>>>(P);
 }
 
 }  // namespace emc

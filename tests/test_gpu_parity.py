@@ -385,3 +385,20 @@ def test_obs_buffer_matches_dicts(emc):
     for e, d in enumerate(dicts):
         for k, v in d.items():
             assert np.array_equal(np.asarray(buf[k][e]), np.asarray(v)), (e, k)
+
+
+def test_production_runs_are_reproducible(emc):
+    """Two identical production (FP32) runs of nanowires large enough that
+    hundreds of electrons are refilled per period give identical integer
+    tallies and subcell charge: nothing in the step depends on thread
+    timing."""
+    cfgs = [W.nanowire(n_particles=50_000, Vd=float(v), seed=110 + v) for v in (5, 20)]
+    out = []
+    for _ in range(2):
+        with emc.Context(cfgs) as ctx:
+            ctx.emc_step(100)
+            out.append((ctx.emc_tally(emc.TALLY_EVENTS), ctx.emc_tally(emc.TALLY_CROSSINGS),
+                        ctx.emc_tally(emc.TALLY_CHARGE), ctx.emc_tally(emc.TALLY_HEAT)))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    assert out[0][1][:, 2:].sum() > 100  # electrons were refilled

@@ -353,7 +353,8 @@ __device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, const K
 template <typename Real>
 struct QEntry {
     Part<Real> q;
-    Real u1, u2, u3;
+    Real u1;
+    uint32_t r2, r3;  // Philox words of the final-state uniforms (converted only for real scatterings)
     Real beta2;          // screening of the subcell's temperature
     const Real* ig0;     // 1/Gamma0 per valley used for the next flight time
     int mech;
@@ -369,8 +370,8 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
     const U4 r = q.draw();
     Real u0 = u01<Real>(r.a);
     Q.u1 = u01<Real>(r.b);
-    Q.u2 = u01<Real>(r.c);
-    Q.u3 = u01<Real>(r.d);
+    Q.r2 = r.c;
+    Q.r3 = r.d;
     const int v = q.v;
     const Real E = q.E;
     Q.beta2 = ph.beta2;
@@ -434,7 +435,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
 {
     Part<Real>& q = Q.q;
     const int mech = Q.mech, v = q.v;
-    const Real E = q.E, u2 = Q.u2;
+    const Real E = q.E, u2 = u01<Real>(Q.r2);
     int j = v;
     Real Ep;
     if (mech == 0 || mech == 3) {
@@ -466,7 +467,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
         rel = false;
     }
     Real sp, cp;
-    Mth<Real>::sincos2pi_u(Q.u3, &sp, &cp);
+    Mth<Real>::sincos2pi_u(u01<Real>(Q.r3), &sp, &cp);
     const Real st = Mth<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
     Real dx, dy, dz;
     if (rel) {
@@ -652,7 +653,7 @@ __device__ __forceinline__ void flush_window(const DevParams& P, BlockTally* bt)
 }
 
 template <typename Real, bool NW>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     k_flight(const DevParams P, const KConst<Real> K, int n_steps, int count_charge)
 {
     extern __shared__ __align__(16) unsigned char sm[];

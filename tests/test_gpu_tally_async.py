@@ -74,3 +74,22 @@ def test_reset_and_pipelined_loop(emc):
     assert len(got) == steps
     for (h0, c0), (h1, c1) in zip(ref, got):
         assert np.array_equal(h0, h1) and np.array_equal(c0, c1)
+
+
+def test_device_destination(emc):
+    """With a device destination the packed tally lands in device memory
+    (here a torch tensor on the context's stream) and equals the host read."""
+    cfgs = [W.nanowire(n_particles=2000, nx=10, Lx=100e-9, Vd=float(v), seed=120 + v) for v in (1, 2)]
+    st = torch.cuda.Stream()
+    with emc.Context(cfgs, stream=st.cuda_stream) as ctx:
+        ctx.emc_step(20)
+        heat_d = torch.empty((2, ctx.n_cell, 2), dtype=torch.int64, device="cuda")
+        hj_d = torch.empty((2, ctx.n_cell), dtype=torch.float64, device="cuda")
+        obs_d = torch.empty(2 * emc.emc.OBS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        ctx.emc_tally_async(emc.TALLY_HEAT, heat_d.data_ptr(), device=True)
+        ctx.emc_tally_async(emc.TALLY_HEAT_J, hj_d.data_ptr(), device=True)
+        ctx.emc_tally_async(emc.TALLY_OBS, obs_d.data_ptr(), device=True)
+        st.synchronize()
+        assert np.array_equal(heat_d.cpu().numpy(), ctx.emc_tally(emc.TALLY_HEAT))
+        assert np.array_equal(hj_d.cpu().numpy(), ctx.emc_tally(emc.TALLY_HEAT_J))
+        obs_equal(obs_d.cpu().numpy().view(emc.emc.OBS_DTYPE), ctx.emc_tally(emc.TALLY_OBS))

@@ -445,6 +445,14 @@ def run_emc(args, world: int, rank: int, local: int):
         e2e_s = time.perf_counter() - w0
         ev2 = int(ctx.emc_tally(emc.TALLY_EVENTS, reset=True).sum())
     heat, cross = bufs[0][1], bufs[0][2]
+    # drain current of every bias point over the end-to-end window (the
+    # crossings accumulate from the reset before the loop): the I-V curve
+    last = bufs[(n_e2e - 1) % 2][2]
+    window_s = n_e2e * steps * cfgs[0]["dt"]
+    iv = []
+    for e, c in enumerate(cfgs):
+        w = c["Nd"] * c["Lx"] * c["Ly"] * c["Lz"] / c["n_particles"]
+        iv.append([c["Vd"], 1e6 * 1.602176634e-19 * w * float(last[e][1] - last[e][3]) / window_s])
     h2d = E * 3 * 8
     d2h = E * 128 + heat.nbytes + cross.nbytes
 
@@ -506,6 +514,8 @@ def run_emc(args, world: int, rank: int, local: int):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"],
                    "samples": clocks["samples"]},
         "gpu_launches": launches,
+        "iv_curve": {"unit": "[V_d (V), I_d (uA) of the half wire]", "window_fs": n_e2e * steps,
+                     "points": [[v, round(i, 3)] for v, i in iv]} if world == 1 else None,
         "batched_mixed": mixed,
         "surrogate_vs_plain_mc": et,
     }

@@ -69,10 +69,16 @@ def workload_desc(n_particles: int) -> dict:
 
 
 def kernel_sha() -> str:
+    """Hash of the flight kernel's sources (common.cuh + kernels.cuh) with
+    comments and blank lines removed: edits of comments keep a committed
+    ncu measurement valid, any change of code invalidates it."""
+    import re
     h = hashlib.sha256()
     for f in ("common.cuh", "kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_1707_09073_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1707_09073_gb300", "csrc", f)) as fh:
+            src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = [re.sub(r"//.*$", "", line).rstrip() for line in src.splitlines()]
+        h.update("\n".join(line for line in code if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

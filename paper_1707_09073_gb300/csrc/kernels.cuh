@@ -346,10 +346,11 @@ __device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, const K
 // One Philox call per scattering: u0 picks the mechanism against the
 // cumulative table row of the current energy bin (lower bin edge; above the
 // last entry = self-scattering), u2/u3 the final direction, u1 the next
-// flight time -ln(u1)/Gamma0 of the final valley.  Split in two so that the
-// block can compact the real scatterings before the final-state code.
+// flight time -ln(u1)/Gamma0 of the final valley.  Split in two: the
+// mechanism choice runs for every scattering, the final state only for real
+// ones (the words of u2/u3 are kept raw until then).
 
-// A queued scattering: the particle plus the draws of its Philox call.
+// A scattering in progress: the particle plus the draws of its Philox call.
 template <typename Real>
 struct QEntry {
     Part<Real> q;

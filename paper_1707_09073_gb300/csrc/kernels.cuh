@@ -11,6 +11,7 @@
 // net energy handed to phonons.
 #pragma once
 #include <map>
+#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -29,7 +30,8 @@ struct Mth<float> {
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
     // -ln(u) of a uniform in (0,1) for a flight time: never negative
     static __device__ __forceinline__ float neglog_u(float u) { return fmaxf(0.f, -__logf(u)); }
-    static __device__ __forceinline__ float pow_(float b, float e) { return exp2f(e * log2f(b)); }
+    // hardware log2 approximation: the FP32 build's angles need no more
+    static __device__ __forceinline__ float pow_(float b, float e) { return exp2f(e * __log2f(b)); }
     static __device__ __forceinline__ void sincospi_(float x, float* s, float* c) { sincospif(x, s, c); }
     // sin and cos of 2 pi u, u in (0,1): evaluated at 2 pi (u - 1/2) in (-pi, pi)
     // where the hardware approximation is accurate, then negated
@@ -402,9 +404,16 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
                     : (b < nbs) ? tab_s + ((size_t)v * nbs + b) * NM : tab_g + ((size_t)v * K.nb + b) * NM;
     int mech = -1;
     if (u0 < row[NM - 1]) {
+        // the row (NM = 10 entries) as five aligned pairs
+        using V2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+        const V2* r2 = reinterpret_cast<const V2*>(row);
+        int cnt = 0;
 #pragma unroll
-        for (int m = 0; m < NM; ++m)
-            if (mech < 0 && u0 < row[m]) mech = m;
+        for (int m = 0; m < NM / 2; ++m) {
+            const V2 pr = r2[m];
+            cnt += (pr.x <= u0) + (pr.y <= u0);
+        }
+        mech = cnt;
     }
     if (mech >= 0) {
         // final energy; a channel that cannot conserve energy counts as self

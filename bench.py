@@ -82,18 +82,28 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic() -> float | None:
-    """DRAM bytes per flight launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def committed_profile() -> dict | None:
+    """The committed ncu figures of the flight kernel (DRAM bytes per launch,
+    issue-slot and lane utilisation), if taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "flight_traffic.txt")
     try:
         with open(p) as f:
             d = json.load(f)
         if d.get("kernel_sha") == kernel_sha():
-            return float(d["dram_bytes_per_launch"])
-    except (OSError, ValueError, KeyError):
+            return d
+    except (OSError, ValueError):
         pass
     return None
+
+
+def committed_traffic() -> float | None:
+    """DRAM bytes per flight launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    d = committed_profile()
+    try:
+        return float(d["dram_bytes_per_launch"]) if d else None
+    except (KeyError, TypeError, ValueError):
+        return None
 
 
 def load_peaks() -> dict:
@@ -478,6 +488,9 @@ def run_emc(args, world: int, rank: int, local: int):
     peak_max = N_SM * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "Tops/s", "frac": achieved / peak_max,
             "traffic": committed_traffic(), "kernel": "k_flight<float, nanowire>",
+            "ncu_same_source": {k: v for k, v in (committed_profile() or {}).items()
+                                if k in ("issue_active_frac", "lanes_active_per_instruction",
+                                         "fp32_pipe_cycles_active_frac", "warps_active_frac")} or None,
             "peak_basis": "152 SMs x 128 lanes x %.0f MHz max SM clock (lane operations/s)" % peaks.get("sm_max_mhz", 2070.0),
             "frac_at_sampled_clock": achieved / (N_SM * LANES_PER_SM * clk * 1e6 / 1e12),
             "flight_share_of_step": flight_ms / ms if ms > 0 else None,

@@ -242,7 +242,7 @@ def electrothermal_comparison(args, stream) -> dict:
     Carlo from a uniform 300 K start vs the surrogate warm start (surrogate
     trained on this library's own bulk Monte Carlo data, its data and
     training time counted separately).  Peak temperature rises are compared
-    at convergence (the Monte Carlo stays the judge)."""
+    at convergence, where the Monte Carlo decides the result."""
     import numpy as np
     import paper_1707_09073_gb300 as emc
     from paper_1707_09073_gb300 import electrothermal as ET

@@ -10,7 +10,7 @@ Surrogate-corrected iteration: after each Monte Carlo run the surrogate's
 drift velocity v_d(E, T) predicts how the heat of every subcell changes with
 its temperature at its Monte Carlo field, and the Fourier solve is iterated
 with that corrected heat to a self-consistent temperature field before the
-next Monte Carlo run; the Monte Carlo remains the judge of the result.
+next Monte Carlo run; the Monte Carlo iteration alone decides the result.
 """
 from __future__ import annotations
 

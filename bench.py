@@ -398,6 +398,7 @@ def run_emc(args, world: int, rank: int, local: int):
     cfgs = sweep_configs(rank, n_part, **tune)
     E = len(cfgs)
     ctx = emc.Context(cfgs, stream=stream.cuda_stream)
+    n_slots_ctx = ctx.capacity
     steps = STEPS_PER_POISSON
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -484,10 +485,16 @@ def run_emc(args, world: int, rank: int, local: int):
     # roofline of the dominant kernel (flight): lane-operation issue rate
     per_launch_ops = (OPS_REAL * real + OPS_SELF * selfe + OPS_STEP * psteps) / max(world, 1) / max(flight_launches, 1)
     avg_s = flight_ms * 1e-3 / max(flight_launches, 1)
+    n_slots = n_slots_ctx
     achieved = per_launch_ops / avg_s / 1e12
     peak_max = N_SM * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "Tops/s", "frac": achieved / peak_max,
             "traffic": committed_traffic(), "kernel": "k_flight<float, nanowire>",
+            "hbm_view": {"algorithmic_bytes_per_launch": 84 * n_slots,
+                         "achieved_gbs": 84 * n_slots / avg_s / 1e9,
+                         "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                         "frac": 84 * n_slots / avg_s / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                         "basis": "84 B of particle state read and written per slot per launch"},
             "ncu_same_source": {k: v for k, v in (committed_profile() or {}).items()
                                 if k in ("issue_active_frac", "lanes_active_per_instruction",
                                          "fp32_pipe_cycles_active_frac", "warps_active_frac")} or None,

@@ -61,3 +61,24 @@ def test_reference_arm_only_on_rank_0(capsys):
         steps, warmup = 1, 3
     assert bench.run_reference(A(), world=2, rank=1) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_under_torchrun_two_ranks(tmp_path):
+    """bench.py --impl reference launched as the multi-GPU driver launches it
+    (torch.distributed.run, two ranks; gloo here): rank 0 alone prints one
+    JSON line, both ranks exit 0."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, EMC_BENCH_BACKEND="gloo", OMP_NUM_THREADS="1")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr=127.0.0.1", f"--master-port={_free_port()}", "bench.py", "--impl", "reference",
+           "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"

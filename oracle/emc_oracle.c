@@ -25,6 +25,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* CODATA 2018 exact / recommended values */
 #define Q_E   1.602176634e-19
@@ -57,6 +60,7 @@ struct orc_sim {
     double bbeta2[151], bkT[151];
     double g0e[ORC_NV];      /* Gamma0 of the ensemble (maximum over the bins in use) */
     int *cbin;               /* [ncell] */
+    int threads;             /* particle-loop threads (1: the plain serial loop) */
 };
 
 /* ---------------------------------------------------------------- Philox */
@@ -395,16 +399,16 @@ static void diffuse_k(orc_sim* s, int64_t p, int ax, double sn, const double u[4
 /* Contacts (absorb at x < 0 / x > Lx), plane A (y = 0, always specular), and
  * the outer side / bottom / top walls (specular with probability p, else
  * diffuse).  Returns 1 if the particle left through a contact. */
-static int walls(orc_sim* s, int64_t p)
+static int walls(orc_sim* s, int64_t p, orc_tallies* t)
 {
     if (s->x[p] < 0.0) {
         s->alive[p] = 0;
-        s->t.crossings[0]++;
+        t->crossings[0]++;
         return 1;
     }
     if (s->x[p] > s->c.Lx) {
         s->alive[p] = 0;
-        s->t.crossings[1]++;
+        t->crossings[1]++;
         return 1;
     }
     double u[4];
@@ -436,7 +440,7 @@ static int walls(orc_sim* s, int64_t p)
 }
 
 /* -------------------------------------------------------------- scatter */
-static void scatter(orc_sim* s, int64_t p)
+static void scatter(orc_sim* s, int64_t p, orc_tallies* t, uint64_t* events)
 {
     double u[4];
     draw4(s, p, u);
@@ -447,7 +451,7 @@ static void scatter(orc_sim* s, int64_t p)
     int b;
     if (fb >= (double)s->nb) {
         b = s->nb - 1;
-        s->t.overflow++;
+        t->overflow++;
     } else {
         b = (int)fb;
     }
@@ -468,7 +472,7 @@ static void scatter(orc_sim* s, int64_t p)
             acc += orc_rate(s, v, m, E) / s->gamma0[v];
             if (mech < 0 && u[0] < acc) mech = m;
         }
-        if (acc > 1.0) s->t.overflow++;
+        if (acc > 1.0) t->overflow++;
     } else {
         for (int m = 0; m < ORC_NM; ++m)
             if (u[0] < C[m]) {
@@ -488,7 +492,7 @@ static void scatter(orc_sim* s, int64_t p)
             Ep = E + (((mech - 4) % 2) == 0 ? s->hw_iv : -s->hw_iv) - (s->Ec[j] - s->Ec[v]);
         }
         if (!(Ep > 0.0)) {
-            s->t.rejected++;
+            t->rejected++;
             mech = -1;
         } else {
             double k = sqrt(k2);
@@ -515,10 +519,10 @@ static void scatter(orc_sim* s, int64_t p)
             s->kz[p] = kp * dir[2];
             s->valley[p] = j;
             vn = j;
-            s->events[((size_t)cell_of(s, p) * ORC_NV + v) * ORC_NM + mech]++;
+            events[((size_t)cell_of(s, p) * ORC_NV + v) * ORC_NM + mech]++;
         }
     }
-    if (mech < 0) s->t.self_events[v]++;
+    if (mech < 0) t->self_events[v]++;
     s->tr[p] = -log(u[1]) / (s->tmode ? s->g0e[vn] : s->gamma0[vn]);
 }
 
@@ -698,6 +702,7 @@ orc_sim* orc_create(const orc_config* cfg)
 {
     orc_sim* s = calloc(1, sizeof(orc_sim));
     s->c = *cfg;
+    s->threads = 1;
     s->nb = cfg->n_bins;
     s->ncell = cfg->geometry == 1 ? cfg->nx * cfg->ny * cfg->nz : 1;
     for (int v = 0; v < ORC_NV; ++v) {
@@ -816,36 +821,83 @@ void orc_set_bias(orc_sim* s, double Vs, double Vd, double Vg)
 }
 
 /* ------------------------------------------------------------------ run */
+/* One time step of particle p: flights and scatterings until the step ends,
+ * then the particle-step sample.  Tallies go to t / events. */
+static void step_particle(orc_sim* s, int64_t p, orc_tallies* t, uint64_t* events)
+{
+    const int nw = s->c.geometry == 1;
+    const double* F = nw ? s->Ef + 3 * (size_t)cell_of(s, p) : s->c.field;
+    double tleft = s->c.dt;
+    for (;;) {
+        if (s->tr[p] >= tleft) {
+            drift(s, p, F, tleft);
+            s->tr[p] -= tleft;
+            if (nw) walls(s, p, t);
+            break;
+        }
+        drift(s, p, F, s->tr[p]);
+        tleft -= s->tr[p];
+        if (nw && walls(s, p, t)) break;
+        scatter(s, p, t, events);
+    }
+    if (!s->alive[p]) return;
+    int v = s->valley[p];
+    double k[3] = {s->kx[p], s->ky[p], s->kz[p]};
+    double E = energy_k2(s, v, k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    double f = HBAR / (s->m[v] * (1.0 + 2.0 * s->a[v] * E));
+    for (int i = 0; i < 3; ++i) t->sum_v[i] += f * k[i];
+    t->sum_E += E;
+    t->sum_Etot += E + s->Ec[v];
+    t->valley_steps[v]++;
+    t->n_samples++;
+}
+
+/* add the per-step tallies of b into a */
+static void add_tallies(orc_tallies* a, const orc_tallies* b)
+{
+    for (int i = 0; i < ORC_NV; ++i) {
+        a->self_events[i] += b->self_events[i];
+        a->valley_steps[i] += b->valley_steps[i];
+    }
+    a->overflow += b->overflow;
+    a->rejected += b->rejected;
+    for (int i = 0; i < 4; ++i) a->crossings[i] += b->crossings[i];
+    a->n_samples += b->n_samples;
+    for (int i = 0; i < 3; ++i) a->sum_v[i] += b->sum_v[i];
+    a->sum_E += b->sum_E;
+    a->sum_Etot += b->sum_Etot;
+}
+
+/* Particles are independent within a step (each has its own random stream
+ * and the field changes only between steps), so the particle loop may run on
+ * several threads.  Thread 0 accumulates into the simulation's own tallies,
+ * which makes one thread exactly the plain serial loop; every other thread
+ * keeps its own partial tallies, added in thread order after each step
+ * (integer tallies are then identical for any thread count; floating sums
+ * differ only by the order of additions). */
 void orc_run(orc_sim* s, int64_t n_steps)
 {
     const int nw = s->c.geometry == 1;
+    const int nt = s->threads > 1 ? s->threads : 1;
+    const size_t nev = (size_t)s->ncell * ORC_NV * ORC_NM;
+    orc_tallies* pt = calloc((size_t)nt, sizeof(orc_tallies));
+    uint64_t** pev = calloc((size_t)nt, sizeof(uint64_t*));
+    pev[0] = s->events;
+    for (int i = 1; i < nt; ++i) pev[i] = calloc(nev, sizeof(uint64_t));
     for (int64_t st = 0; st < n_steps; ++st) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(static)
+#endif
         for (int64_t p = 0; p < s->cap; ++p) {
-            if (!s->alive[p]) continue;
-            const double* F = nw ? s->Ef + 3 * (size_t)cell_of(s, p) : s->c.field;
-            double tleft = s->c.dt;
-            for (;;) {
-                if (s->tr[p] >= tleft) {
-                    drift(s, p, F, tleft);
-                    s->tr[p] -= tleft;
-                    if (nw) walls(s, p);
-                    break;
-                }
-                drift(s, p, F, s->tr[p]);
-                tleft -= s->tr[p];
-                if (nw && walls(s, p)) break;
-                scatter(s, p);
-            }
-            if (!s->alive[p]) continue;
-            int v = s->valley[p];
-            double k[3] = {s->kx[p], s->ky[p], s->kz[p]};
-            double E = energy_k2(s, v, k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
-            double f = HBAR / (s->m[v] * (1.0 + 2.0 * s->a[v] * E));
-            for (int i = 0; i < 3; ++i) s->t.sum_v[i] += f * k[i];
-            s->t.sum_E += E;
-            s->t.sum_Etot += E + s->Ec[v];
-            s->t.valley_steps[v]++;
-            s->t.n_samples++;
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            if (s->alive[p]) step_particle(s, p, tid == 0 ? &s->t : &pt[tid], pev[tid]);
+        }
+        for (int i = 1; i < nt; ++i) {
+            add_tallies(&s->t, &pt[i]);
+            memset(&pt[i], 0, sizeof(orc_tallies));
         }
         s->t.steps_done++;
         if (nw && (s->t.steps_done % s->c.steps_per_poisson) == 0) {
@@ -855,10 +907,53 @@ void orc_run(orc_sim* s, int64_t n_steps)
             solve_field(s);
         }
     }
+    for (int i = 1; i < nt; ++i) {
+        for (size_t j = 0; j < nev; ++j) s->events[j] += pev[i][j];
+        free(pev[i]);
+    }
+    free(pev);
+    free(pt);
     int64_t alive = 0;
     for (int64_t p = 0; p < s->cap; ++p) alive += s->alive[p];
     s->t.n_alive = alive;
     if (!nw) s->charge[0] = alive;
+}
+
+void orc_set_threads(orc_sim* s, int n) { s->threads = n > 1 ? n : 1; }
+
+/* ------------------------------------------------------------ test hooks */
+/* One free flight of a lone electron in valley v from wave vector k0 and
+ * position r0 under the field F (V/m) for time t: the nanowire's position
+ * update (particle slot 0 of s serves as scratch). */
+void orc_test_drift(orc_sim* s, int v, const double k0[3], const double r0[3], const double F[3], double t,
+                    double k1[3], double r1[3])
+{
+    s->valley[0] = v;
+    s->kx[0] = k0[0]; s->ky[0] = k0[1]; s->kz[0] = k0[2];
+    s->x[0] = r0[0]; s->y[0] = r0[1]; s->z[0] = r0[2];
+    drift(s, 0, F, t);
+    k1[0] = s->kx[0]; k1[1] = s->ky[0]; k1[2] = s->kz[0];
+    r1[0] = s->x[0]; r1[1] = s->y[0]; r1[2] = s->z[0];
+}
+
+/* The wall and contact treatment of a lone electron at position r0 with wave
+ * vector k0 whose random stream (key: the ensemble seed and particle id 0)
+ * stands at counter ctr.  Returns 1 if it left through a contact; r1, k1 and
+ * *ctr_out receive the state after the walls (slot 0 of s is scratch). */
+int orc_test_walls(orc_sim* s, const double r0[3], const double k0[3], uint64_t ctr, double r1[3], double k1[3],
+                   uint64_t* ctr_out)
+{
+    orc_tallies t;
+    memset(&t, 0, sizeof t);
+    s->alive[0] = 1;
+    s->kx[0] = k0[0]; s->ky[0] = k0[1]; s->kz[0] = k0[2];
+    s->x[0] = r0[0]; s->y[0] = r0[1]; s->z[0] = r0[2];
+    s->ctr[0] = ctr;
+    int out = walls(s, 0, &t);
+    k1[0] = s->kx[0]; k1[1] = s->ky[0]; k1[2] = s->kz[0];
+    r1[0] = s->x[0]; r1[1] = s->y[0]; r1[2] = s->z[0];
+    *ctr_out = s->ctr[0];
+    return out;
 }
 
 void orc_get_tallies(const orc_sim* s, orc_tallies* out) { *out = s->t; }

@@ -71,6 +71,9 @@ int orc_ncell(const orc_sim* s);
 double orc_rate(const orc_sim* s, int valley, int mech, double E_J);
 void orc_get_tables(const orc_sim* s, double* table /* [NV][NB][NM] */, double* gamma0 /* [NV] */);
 void orc_run(orc_sim* s, int64_t n_steps);
+/* threads of the particle loop in orc_run (default 1; integer tallies do not
+ * depend on it) */
+void orc_set_threads(orc_sim* s, int n);
 void orc_get_tallies(const orc_sim* s, orc_tallies* out);
 void orc_get_events(const orc_sim* s, uint64_t* ev /* [ncell][NV][NM] */);
 void orc_get_charge(const orc_sim* s, int64_t* ch /* [ncell] */);
@@ -86,6 +89,13 @@ void orc_sample_initial_energy(const orc_sim* s, int64_t n, double* E);
 double orc_cos_pop(double k, double kp, double u);
 double orc_cos_imp(double k, double beta2, double u);
 void orc_rotate(const double n[3], double ct, double ph, double out[3]);
+
+/* test hooks (slot 0 of s is overwritten): one free flight, one pass
+ * through the walls and contacts */
+void orc_test_drift(orc_sim* s, int v, const double k0[3], const double r0[3], const double F[3], double t,
+                    double k1[3], double r1[3]);
+int orc_test_walls(orc_sim* s, const double r0[3], const double k0[3], uint64_t ctr, double r1[3], double k1[3],
+                   uint64_t* ctr_out);
 
 /* Poisson on the subcell grid: charge density rho (C/m^3) -> phi (V). */
 int orc_poisson(const orc_config* cfg, const double* rho, double* phi, double tol, int maxit);

@@ -23,13 +23,14 @@ Q_E = 1.602176634e-19
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree;
+    OpenMP for the optional particle-parallel loop, one thread by default)."""
     os.makedirs(BUILD, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in SRC + [os.path.join(HERE, "emc_oracle.h")])
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-o", tmp] + SRC + ["-lm"])
+                               "-ffp-contract=off", "-fopenmp", "-o", tmp] + SRC + ["-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -86,6 +87,10 @@ def lib():
         L.orc_rate.restype = C.c_double
         L.orc_get_tables.argtypes = [P, dp, dp]
         L.orc_run.argtypes = [P, C.c_int64]
+        L.orc_set_threads.argtypes = [P, C.c_int]
+        L.orc_test_drift.argtypes = [P, C.c_int, dp, dp, dp, C.c_double, dp, dp]
+        L.orc_test_walls.argtypes = [P, dp, dp, C.c_uint64, dp, dp, C.POINTER(C.c_uint64)]
+        L.orc_test_walls.restype = C.c_int
         L.orc_get_tallies.argtypes = [P, C.POINTER(OrcTallies)]
         L.orc_get_events.argtypes = [P, C.POINTER(C.c_uint64)]
         L.orc_get_charge.argtypes = [P, C.POINTER(C.c_int64)]
@@ -149,16 +154,48 @@ def u01(x: int) -> float:
     return lib().orc_u01(x)
 
 
-class Sim:
-    """One ensemble simulated by the oracle."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
-    def __init__(self, cfg: dict):
+
+class Sim:
+    """One ensemble simulated by the oracle.  threads > 1 runs the particle
+    loop on that many threads (integer tallies are the same for any count)."""
+
+    def __init__(self, cfg: dict, threads: int = 1):
         self.cfg = dict(cfg)
         self._c = make_config(cfg)
         self.h = lib().orc_create(C.byref(self._c))
         self.ncell = lib().orc_ncell(self.h)
         self.nb = cfg["n_bins"]
         self.cap = max(cfg["capacity"], cfg["n_particles"])
+        self.threads = 1
+        if threads != 1:
+            self.set_threads(threads)
+
+    def set_threads(self, n: int):
+        self.threads = max(1, int(n))
+        lib().orc_set_threads(self.h, self.threads)
+
+    def test_drift(self, valley: int, k0, r0, F, t: float):
+        """One free flight of a lone electron (test hook; overwrites slot 0)."""
+        k0 = np.ascontiguousarray(k0, dtype=float); r0 = np.ascontiguousarray(r0, dtype=float)
+        F = np.ascontiguousarray(F, dtype=float)
+        k1 = np.zeros(3); r1 = np.zeros(3)
+        lib().orc_test_drift(self.h, int(valley), _ptr(k0), _ptr(r0), _ptr(F), float(t), _ptr(k1), _ptr(r1))
+        return k1, r1
+
+    def test_walls(self, r0, k0, ctr: int):
+        """The walls and contacts applied to a lone electron (test hook;
+        overwrites slot 0): (absorbed, r1, k1, counter after)."""
+        r0 = np.ascontiguousarray(r0, dtype=float); k0 = np.ascontiguousarray(k0, dtype=float)
+        r1 = np.zeros(3); k1 = np.zeros(3); c1 = C.c_uint64()
+        out = lib().orc_test_walls(self.h, _ptr(r0), _ptr(k0), int(ctr), _ptr(r1), _ptr(k1), C.byref(c1))
+        return bool(out), r1, k1, int(c1.value)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -64,6 +64,7 @@ def workload_desc(n_particles: int) -> dict:
         "ensembles": 21,
         "particles_per_ensemble": n_particles,
         "step": "one Poisson period (10 x 1 fs) of all 21 bias points",
+        "start": "timed after an untimed start-up transient (--prewarm-ps of simulated time) and the warm-up steps",
         "l2": "inputs larger than L2: particle state %.0f MB > 129 MB L2" % (21 * n_particles * 44 / 1e6),
     }
 
@@ -401,6 +402,9 @@ def run_emc(args, world: int, rank: int, local: int):
     n_slots_ctx = ctx.capacity
     steps = STEPS_PER_POISSON
     with torch.cuda.stream(stream):
+        # untimed: the electrons first leave the start-up transient (the
+        # event rate of the first picoseconds is inflated)
+        ctx.emc_step(int(round(args.prewarm_ps * 1000)))
         for _ in range(args.warmup):
             ctx.emc_step(steps)
         ctx.emc_tally(emc.TALLY_OBS, reset=True)
@@ -556,6 +560,8 @@ def main():
     ap.add_argument("--impl", default="emc", choices=["emc", "reference"])
     ap.add_argument("--particles", type=int, default=200_000)
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--prewarm-ps", type=float, default=8.0,
+                    help="untimed simulated time before the warm-up steps (the start-up transient)")
     ap.add_argument("--cpu-particles", type=int, default=200_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -80,10 +80,9 @@ struct DevParams {
     double Lx, Ly, Lz, dx, dy, dz, p_spec;
     double dt;                // fs
     // tallies (accumulating)
-    unsigned long long* events;   // [E][NV][NM]
+    unsigned long long* events;   // [E][C][NV][NM] real events per subcell (bulk: C = 1)
     unsigned long long* cnt;      // [E][NCNT]
     double* sums;                 // [E][NSUM]
-    long long* heat;              // [E][C][2]
     int* charge;                  // [E][C]
     long long* alive;             // [E] live particles (never reset)
     // per-subcell temperature (null cell_bin: one temperature per ensemble)

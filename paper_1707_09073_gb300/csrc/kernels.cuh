@@ -117,21 +117,14 @@ __device__ __forceinline__ void tally_cnt(BlockTally* bt, const DevParams& P, in
     }
 }
 
-// Atomic add of d to base[key] from the lanes currently executing together:
-// lanes with the same key (particles of one subcell after sorting) combine
-// their contributions and one of them issues the atomic.
-__device__ __forceinline__ void agg_add_ll(long long* base, int key, long long d)
+// Increment of base[idx] by the lanes currently executing together: lanes
+// with the same counter (particles of one subcell after sorting, scattering
+// by the same mechanism) are counted together and one of them issues the
+// atomic.
+__device__ __forceinline__ void agg_inc_u64(unsigned long long* base, unsigned long long idx)
 {
-    const unsigned peers = __match_any_sync(__activemask(), key);
-    const int leader = __ffs(peers) - 1;
-    long long sum = d;
-    if (peers != (1u << leader)) {
-        // gather the peers' contributions, lowest lane first
-        sum = 0;
-        for (unsigned m = peers; m; m &= m - 1u) sum += __shfl_sync(peers, d, __ffs(m) - 1);
-    }
-    if ((threadIdx.x & 31) == leader && sum != 0)
-        atomicAdd(reinterpret_cast<unsigned long long*>(base + key), (unsigned long long)sum);
+    const unsigned peers = __match_any_sync(__activemask(), idx);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(base + idx, (unsigned long long)__popc(peers));
 }
 
 __device__ __forceinline__ void agg_add_i(int* base, int key)
@@ -508,16 +501,17 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
     q.kz = kp * dz;
     q.E = Ep;
     q.f = ph.vk[j] / (Real(1) + Real(2) * ph.alpha[j] * Ep);
-    const int w = q.e - e_base;
-    if (w >= 0 && w < WE)
-        atomicAdd(&bt->ev[w][v * NM + mech], 1u);
-    else
-        atomicAdd(&P.events[((size_t)q.e * NV + v) * NM + mech], 1ull);
-    if (NW && mech != 0 && mech != 3) {
+    if (NW) {
+        // real events per (subcell, valley, mechanism): the subcell heat map
+        // (net phonon emission) and the mechanism statistics both follow
         const int c = cell_of<Real>(K, q.x, q.y, q.z);
-        // net emission: mech 1 absorbs, 2 emits; 4+2j absorbs, 5+2j emits
-        const long long d = (mech == 1) ? -1 : (mech == 2 ? 1 : ((mech & 1) ? 1 : -1));
-        agg_add_ll(P.heat, (q.e * K.ncell + c) * 2 + (mech <= 2 ? 0 : 1), d);
+        agg_inc_u64(P.events, ((unsigned long long)q.e * K.ncell + c) * (NV * NM) + v * NM + mech);
+    } else {
+        const int w = q.e - e_base;
+        if (w >= 0 && w < WE)
+            atomicAdd(&bt->ev[w][v * NM + mech], 1u);
+        else
+            atomicAdd(&P.events[((size_t)q.e * NV + v) * NM + mech], 1ull);
     }
     q.v = j;
     q.tr = Mth<Real>::neglog_u(Q.u1) * Q.ig0[j];
@@ -643,7 +637,7 @@ __device__ __forceinline__ void flush_window(const DevParams& P, BlockTally* bt)
 {
     for (int i = threadIdx.x; i < WE * NV * NM; i += blockDim.x) {
         const int w = i / (NV * NM), j = i - w * NV * NM;
-        const unsigned int n = bt->ev[w][j];
+        const unsigned int n = bt->ev[w][j];  // bulk only (one subcell per ensemble)
         if (n && w < P.n_ens) atomicAdd(&P.events[(size_t)w * NV * NM + j], (unsigned long long)n);
     }
     for (int i = threadIdx.x; i < WE * NCNT; i += blockDim.x) {

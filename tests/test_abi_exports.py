@@ -41,7 +41,7 @@ def test_status_codes_and_tally_kinds_match_header(emc):
     codes = dict((k, int(v)) for k, v in re.findall(r"\b(EMC_[A-Z0-9_]+)\s*=\s*(\d+)", h))
     assert codes["EMC_OK"] == 0
     for name in ("TALLY_OBS", "TALLY_EVENTS", "TALLY_HEAT", "TALLY_CHARGE", "TALLY_CROSSINGS", "TALLY_PHI",
-                 "TALLY_FIELD", "TALLY_HEAT_J"):
+                 "TALLY_FIELD", "TALLY_HEAT_J", "TALLY_EVENTS_CELL"):
         assert getattr(emc, name) == codes["EMC_" + name], name
     assert emc.FP32 == codes["EMC_FP32"] and emc.FP64 == codes["EMC_FP64"]
     assert emc.GEOM_BULK == codes["EMC_GEOM_BULK"] and emc.GEOM_NANOWIRE == codes["EMC_GEOM_NANOWIRE"]

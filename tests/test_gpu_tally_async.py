@@ -13,7 +13,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 KINDS = ["TALLY_OBS", "TALLY_EVENTS", "TALLY_HEAT", "TALLY_CHARGE", "TALLY_CROSSINGS", "TALLY_PHI", "TALLY_FIELD",
-         "TALLY_HEAT_J"]
+         "TALLY_HEAT_J", "TALLY_EVENTS_CELL"]
 
 
 def obs_equal(a, dicts):

@@ -42,8 +42,11 @@ typedef enum emc_status {
     EMC_EINVAL = 1,     /* invalid argument or configuration */
     EMC_ENOMEM = 2,     /* device or host allocation failed */
     EMC_ECUDA = 3,      /* a CUDA call failed (message in emc_last_error) */
-    EMC_EOVERFLOW = 4,  /* a bounded loop or buffer limit was hit on the device */
-    EMC_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    EMC_EOVERFLOW = 4,  /* a device-side check failed: a bounded loop or buffer limit
+                           was hit, or a particle's energy was not finite (the message
+                           names the bits of the device error word) */
+    EMC_ETIMEOUT = 5,   /* a bounded device wait gave up (the surrogate's tensor-core
+                           GEMM waits on its mbarriers with an iteration limit) */
     EMC_ESTATE = 6      /* call not valid in the context's current state */
 } emc_status;
 
@@ -122,16 +125,24 @@ typedef struct emc_obs {
  * C = 1 for bulk): */
 enum {
     EMC_TALLY_OBS = 0,       /* emc_obs[E] */
-    EMC_TALLY_EVENTS = 1,    /* uint64[E][3][10] real scattering events (valley, mechanism) */
-    EMC_TALLY_HEAT = 2,      /* int64[E][C][2] net phonon emissions (emitted - absorbed):
-                                [.][0] polar optical, [.][1] intervalley */
+    EMC_TALLY_EVENTS = 1,    /* uint64[E][3][10] real scattering events (valley before the
+                                event, mechanism), summed over the subcells */
+    EMC_TALLY_HEAT = 2,      /* int64[E][C][2] net phonon emissions (emitted - absorbed) per
+                                subcell: [.][0] polar optical, [.][1] intervalley (from the
+                                per-subcell event counts of EMC_TALLY_EVENTS_CELL) */
     EMC_TALLY_CHARGE = 3,    /* int64[E][C] electrons per subcell at the last Poisson update
                                 (bulk: live electrons) */
     EMC_TALLY_CROSSINGS = 4, /* int64[E][4] source out, drain out, source in, drain in */
     EMC_TALLY_PHI = 5,       /* double[E][C] potential, V */
     EMC_TALLY_FIELD = 6,     /* double[E][C][3] field, V/m */
-    EMC_TALLY_HEAT_J = 7     /* double[E][C] net energy emitted to phonons per subcell, J
+    EMC_TALLY_HEAT_J = 7,    /* double[E][C] net energy emitted to phonons per subcell, J
                                 (superparticle weight included) */
+    EMC_TALLY_EVENTS_CELL = 8 /* uint64[E][C][3][10] real scattering events per subcell (the
+                                subcell where the electron scattered; valley before the
+                                event, mechanism); bulk: C = 1.  The electron counts of
+                                the subcells that feed the Poisson update and the energy
+                                exchange with phonons counted per subcell (the Poisson
+                                and heat-generation passages next to Table I) */
 };
 
 /* Create a context holding one ensemble (emc_batch_init with n_ens = 1).
@@ -158,7 +169,9 @@ emc_status emc_step(emc_ctx* ctx, int32_t n_steps);
  * at least the size given above; dst_is_device: 1 = device pointer on the
  * context's device, 0 = host).  Synchronises the context stream.  reset = 1
  * zeroes the accumulating tallies (OBS sums and counts except steps_done and
- * n_alive, EVENTS, HEAT, CROSSINGS) after the copy. */
+ * n_alive, the event counts and with them EVENTS, HEAT, HEAT_J, CROSSINGS)
+ * after the copy.  The first call allocates a small device staging buffer
+ * (the largest tally computed on the device). */
 emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes,
                      int32_t dst_is_device, int32_t reset);
 
@@ -195,16 +208,42 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null,
  * array of about 1.6 MiB owned by the library, so the call performs no
  * cudaMalloc or cudaFree of its own.
  *  - Limit: at most 8192 subcells; larger grids return EMC_EINVAL.
- *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.  The array then stays reserved on every
- *    device that used it until the library is unloaded.
+ *  - The first call in a CUDA context looks the array's device address up
+ *    (cudaGetSymbolAddress) with that context current and keeps it for
+ *    later calls in the same context (a context created anew, e.g. after
+ *    cudaDeviceReset, gets a fresh lookup); make that first call before any
+ *    stream capture.  The array stays reserved on every device that loaded
+ *    the library until the library is unloaded or the context is destroyed.
  *  - All calls share the one array: calls that may overlap on the GPU
  *    (other threads, other streams, other contexts on the same device) race
  *    and must be serialised by the caller.  Each call zeroes the potential
  *    it starts from, so a call never sees the previous call's result. */
 emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null,
                                     const double* bc_volts, double* phi_out_or_null);
+
+/* Checkpoint and resume.  emc_get_state copies the whole simulation state
+ * of the context into the host buffer dst (synchronises the stream):
+ * particle state (wave vector, position, residual flight time, valley and
+ * ensemble tag, Philox counter, id), the id->slot map and free-id bitmaps,
+ * every accumulating tally, the device error word, the terminal voltages,
+ * the potential and field (nanowire), the subcell temperature bins and
+ * Gamma0 (once emc_set_temperature was used), the step count and the sort
+ * phase.  emc_state_size gives the bytes needed (*bytes).  emc_set_state
+ * restores such a blob into a context created from the same ensembles
+ * (same emc_config array; the launch-tuning fields block_size,
+ * steps_per_launch, table_smem_kb and sort_period may differ); continuing
+ * from it gives the run that continuing the saved context would have given.
+ * Layout (host byte order, this library version only): a 72-byte header
+ * (magic "EMCSTATE", version, precision, geometry, temperature mode,
+ * ensembles, subcells, slots, bitmap words, steps done, sort phase,
+ * configuration hash), then the arrays in the order listed above, slot
+ * order, in the context's precision (the wave vector first: k_x of slot 0
+ * starts at byte 72, in 1/nm).  Errors: EMC_EINVAL for a short buffer or a
+ * foreign blob, EMC_ESTATE for a blob of other ensembles or without the
+ * subcell temperatures this context has. */
+emc_status emc_state_size(emc_ctx* ctx, size_t* bytes);
+emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes);
+emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes);
 
 /* Lattice temperature per subcell of ensemble ens (nanowire contexts whose
  * ensembles share one material and doping): T_cells[n] in K, n = the
@@ -285,6 +324,20 @@ emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, f
 emc_status emc_mlp_params(emc_mlp* m, float* dst, const float* src, int64_t* count);
 const char* emc_mlp_last_error(const emc_mlp* m);
 void emc_mlp_destroy(emc_mlp* m);
+
+/* The surrogate attached to a Monte Carlo context (the learned part's calls
+ * on the context itself): emc_surrogate_train creates the context's network
+ * from `net` on the context's stream (replacing an earlier one) and trains
+ * it on the host rows X [n][n_in], Y [n][n_out] exactly as emc_mlp_train;
+ * emc_surrogate_infer evaluates it (host arrays, as emc_mlp_infer);
+ * emc_surrogate_params reads its parameter vector (layout of
+ * emc_mlp_params; dst NULL: *count only).  The network lives until
+ * emc_destroy or the next emc_surrogate_train.  EMC_ESTATE: no network
+ * trained yet. */
+emc_status emc_surrogate_train(emc_ctx* ctx, const emc_mlp_config* net, const float* X, const float* Y, int64_t n,
+                               const emc_train_config* tc, float* loss_history);
+emc_status emc_surrogate_infer(emc_ctx* ctx, const float* X, float* Y, int64_t n);
+emc_status emc_surrogate_params(emc_ctx* ctx, float* dst, int64_t* count);
 
 /* ------------------------------------------------------------------------
  * Thermal side of the electrothermal loop: steady Fourier conduction on the

@@ -64,3 +64,27 @@ def loss_and_grad(theta, sizes, X, Y, norm):
 def predict(theta, sizes, X, norm):
     _, zs = forward(theta, sizes, X, norm)
     return zs[-1] * norm["y_scale"] + norm["y_shift"]
+
+
+def grad_abs_products(theta, sizes, X, Y, norm):
+    """Per parameter, the sum of absolute values of the products that make
+    its gradient, carried through the chain with absolute values:
+    |dz_L| = |2 d / n|, |dz_l| = (|dz_{l+1}| |W_l|) |silu'(z_l)|, and
+    S_W = |dz_{l+1}|^T |h_l|, S_b = sum |dz_{l+1}|.  An element computed with
+    rounded operands of relative precision u errs by at most about
+    (depth) u S (the standard running-error bound of sums of products)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    hs, zs = forward(theta, sizes, X, norm)
+    t = (Y - norm["y_shift"]) / norm["y_scale"]
+    d = zs[-1] - t
+    n = d.size
+    layers = unpack(np.asarray(theta, dtype=np.float64), sizes)
+    out = [None] * len(layers)
+    dz = np.abs(2.0 * d / n)
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        out[l] = (dz.T @ np.abs(hs[l]), dz.sum(axis=0))
+        if l > 0:
+            dz = (dz @ np.abs(W)) * np.abs(dsilu(zs[l - 1]))
+    return np.concatenate([np.concatenate([sW.ravel(), sb]) for sW, sb in out])

@@ -1,8 +1,10 @@
 // libemc host side: the C ABI of include/emc.h, device memory, rate tables,
 // Poisson update and the step loop.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -71,7 +73,7 @@ struct emc_ctx {
     int n_ens = 0, prec = EMC_FP32, geom = EMC_GEOM_BULK;
     int nx = 1, ny = 1, nz = 1, ncell = 1, nb = 0, n_tab = 0, block = 256, spl = 50, K = 10, grid_cap = 1;
     int sort_period = 0;
-    int64_t n_slots = 0, steps_done = 0, launches = 0;
+    int64_t n_slots = 0, steps_done = 0, launches = 0, bits_words = 0;
     double dt_fs = 1.0, dE = 0.002;
     double Lx = 1, Ly = 1, Lz = 1, dx = 1, dy = 1, dz = 1;  // nm
     std::vector<int64_t> off, cap, n0;
@@ -94,7 +96,6 @@ struct emc_ctx {
     double* tab64 = nullptr;
     unsigned long long *events = nullptr, *cnt = nullptr;
     double* sums = nullptr;
-    long long* heat = nullptr;
     int* charge = nullptr;
     long long* alive = nullptr;
     int* d_err = nullptr;
@@ -128,6 +129,8 @@ struct emc_ctx {
     cudaGraphExec_t g_tail_exec = nullptr;
     int64_t g_tail_launches = 0;
     bool use_graph = true;
+    // the context's surrogate network (emc_surrogate_train)
+    emc_mlp* sur = nullptr;
     // flight-kernel timing
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -733,7 +736,7 @@ void fill_params(emc_ctx* ctx)
     P.dx = ctx->dx; P.dy = ctx->dy; P.dz = ctx->dz;
     P.p_spec = ctx->cfg[0].p_specular;
     P.dt = ctx->dt_fs;
-    P.events = ctx->events; P.cnt = ctx->cnt; P.sums = ctx->sums; P.heat = ctx->heat; P.charge = ctx->charge;
+    P.events = ctx->events; P.cnt = ctx->cnt; P.sums = ctx->sums; P.charge = ctx->charge;
     P.alive = ctx->alive;
     P.cell_bin = ctx->cell_bin;
     P.bin_table = ctx->bin_table;
@@ -906,6 +909,18 @@ emc_status build_bins(emc_ctx* ctx)
         for (int cc = 0; cc < ctx->ncell; ++cc) ctx->cell_bin_host[(size_t)e * ctx->ncell + cc] = k;
         for (int v = 0; v < NV; ++v) ctx->ens_g0_host[(size_t)e * NV + v] = ctx->g0_host[(size_t)ctx->tabset[e] * NV + v];
     }
+    // every ensemble's bins and Gamma0 on the device, not only the ensemble
+    // whose temperatures are being set: the flight kernel reads them for all
+    std::vector<Real> gR((size_t)ctx->n_ens * NV), igR((size_t)ctx->n_ens * NV);
+    for (size_t i = 0; i < gR.size(); ++i) {
+        gR[i] = Real(ctx->ens_g0_host[i]);
+        igR[i] = Real(1.0 / ctx->ens_g0_host[i]);
+    }
+    CK(cudaMemcpyAsync(ctx->cell_bin, ctx->cell_bin_host.data(), sizeof(int32_t) * ctx->cell_bin_host.size(),
+                       cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(g0, gR.data(), sizeof(Real) * gR.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ig0, igR.data(), sizeof(Real) * igR.size(), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
 }
 
@@ -968,18 +983,43 @@ size_t tally_bytes(int E, int C, int kind)
     case EMC_TALLY_PHI: return 8ull * E * C;
     case EMC_TALLY_FIELD: return 8ull * E * C * 3;
     case EMC_TALLY_HEAT_J: return 8ull * E * C;
+    case EMC_TALLY_EVENTS_CELL: return 8ull * E * C * NV * NM;
     default: return 0;
     }
 }
 
-// A tally in its ABI layout, computed on the device from the accumulators
-// (the same conversions emc_tally does on the host): observations and
-// crossings per ensemble, subcell charge (bulk: live count), heat in joules
-// (net phonons x energy x superparticle weight), and the zero potential and
-// uniform field of bulk ensembles.  par[E][6] = {hw_lo, hw_iv, w, Fx, Fy, Fz}.
+// bytes of the device staging buffer: the largest tally packed on the device
+size_t stage_bytes(int E, int C)
+{
+    size_t b = 0;
+    for (int k : {EMC_TALLY_OBS, EMC_TALLY_EVENTS, EMC_TALLY_HEAT, EMC_TALLY_CHARGE, EMC_TALLY_CROSSINGS,
+                  EMC_TALLY_PHI, EMC_TALLY_FIELD, EMC_TALLY_HEAT_J})
+        b = std::max(b, tally_bytes(E, C, k));
+    return b;
+}
+
+// A tally in its ABI layout, computed on the device from the accumulators:
+// observations and crossings per ensemble, event counts per ensemble (summed
+// over subcells), subcell charge (bulk: live count), net phonon emissions per
+// subcell and their energy (from the per-subcell event counts: polar optical
+// emissions 2 minus absorptions 1; intervalley emissions 5, 7, 9 minus
+// absorptions 4, 6, 8), and the zero potential and uniform field of bulk
+// ensembles.  par[E][6] = {hw_lo, hw_iv, w, Fx, Fy, Fz}.
+__device__ __forceinline__ void net_phonons(const unsigned long long* ev, long long* pop, long long* iv)
+{
+    long long a = 0, b = 0;
+    for (int v = 0; v < NV; ++v) {
+        const unsigned long long* r = ev + v * NM;
+        a += (long long)r[2] - (long long)r[1];
+        for (int j = 0; j < NV; ++j) b += (long long)r[5 + 2 * j] - (long long)r[4 + 2 * j];
+    }
+    *pop = a;
+    *iv = b;
+}
+
 __global__ void k_tally_pack(int kind, int E, int C, int nw, const unsigned long long* cnt, const double* sums,
-                             const long long* alive, const int* charge, const long long* heat, const double* par,
-                             long long steps_done, void* out)
+                             const long long* alive, const int* charge, const unsigned long long* events,
+                             const double* par, long long steps_done, void* out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (kind == EMC_TALLY_OBS) {
@@ -1008,13 +1048,28 @@ __global__ void k_tally_pack(int kind, int E, int C, int nw, const unsigned long
         o[1] = (int64_t)c[CNT_DRN_OUT];
         o[2] = (int64_t)c[CNT_SRC_IN];
         o[3] = (int64_t)c[CNT_DRN_IN];
+    } else if (kind == EMC_TALLY_EVENTS) {
+        // one thread per (ensemble, valley x mechanism), summing the subcells
+        if (i >= (int64_t)E * NV * NM) return;
+        const int64_t e = i / (NV * NM), j = i - e * (NV * NM);
+        const unsigned long long* ev = events + (size_t)e * C * NV * NM + j;
+        unsigned long long sum = 0;
+        for (int c = 0; c < C; ++c) sum += ev[(size_t)c * NV * NM];
+        static_cast<unsigned long long*>(out)[i] = sum;
     } else if (kind == EMC_TALLY_CHARGE) {
         if (i >= (int64_t)E * C) return;
         static_cast<int64_t*>(out)[i] = nw ? (int64_t)charge[i] : (int64_t)alive[i / C];
-    } else if (kind == EMC_TALLY_HEAT_J) {
+    } else if (kind == EMC_TALLY_HEAT || kind == EMC_TALLY_HEAT_J) {
         if (i >= (int64_t)E * C) return;
-        const double* p = par + 6 * (i / C);
-        static_cast<double*>(out)[i] = ((double)heat[2 * i] * p[0] + (double)heat[2 * i + 1] * p[1]) * kQ * p[2];
+        long long pop, iv;
+        net_phonons(events + (size_t)i * NV * NM, &pop, &iv);
+        if (kind == EMC_TALLY_HEAT) {
+            static_cast<int64_t*>(out)[2 * i] = pop;
+            static_cast<int64_t*>(out)[2 * i + 1] = iv;
+        } else {
+            const double* p = par + 6 * (i / C);
+            static_cast<double*>(out)[i] = ((double)pop * p[0] + (double)iv * p[1]) * kQ * p[2];
+        }
     } else if (kind == EMC_TALLY_PHI) {
         if (i >= (int64_t)E * C) return;
         static_cast<double*>(out)[i] = 0.0;
@@ -1024,6 +1079,16 @@ __global__ void k_tally_pack(int kind, int E, int C, int nw, const unsigned long
     }
 }
 
+bool finite_inputs(const double* charge_or_null, int n, const double* bc)
+{
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(bc[i])) return false;
+    if (charge_or_null)
+        for (int i = 0; i < n; ++i)
+            if (!std::isfinite(charge_or_null[i])) return false;
+    return true;
+}
+
 emc_status check_err(emc_ctx* ctx)
 {
     int h = 0;
@@ -1031,7 +1096,8 @@ emc_status check_err(emc_ctx* ctx)
     CK(cudaStreamSynchronize(ctx->st));
     if (h) {
         char buf[128];
-        snprintf(buf, sizeof buf, "device error word 0x%x (1: flight loop bound, 2: NaN energy, 4: init draws)", h);
+        snprintf(buf, sizeof buf, "device error word 0x%x (1: flight loop bound, 2: non-finite particle energy, "
+                                  "4: initial-energy draws)", h);
         return fail(ctx, EMC_EOVERFLOW, buf);
     }
     return EMC_OK;
@@ -1230,6 +1296,7 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
         ctx->bias[3 * e + 2] = c.Vg;
     }
     ctx->n_slots = o;
+    ctx->bits_words = bo;
     *out = ctx;
 #define CKI(call)                                                                                  \
     do {                                                                                           \
@@ -1249,10 +1316,9 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
     CKI(dalloc(ctx, &ctx->d_seed, n_ens));
     CKI(dalloc(ctx, &ctx->d_tabset, n_ens));
     CKI(dalloc(ctx, &ctx->d_target, n_ens));
-    CKI(dalloc(ctx, &ctx->events, (size_t)n_ens * NV * NM));
+    CKI(dalloc(ctx, &ctx->events, (size_t)n_ens * ctx->ncell * NV * NM));
     CKI(dalloc(ctx, &ctx->cnt, (size_t)n_ens * NCNT));
     CKI(dalloc(ctx, &ctx->sums, (size_t)n_ens * NSUM));
-    CKI(dalloc(ctx, &ctx->heat, (size_t)n_ens * ctx->ncell * 2));
     CKI(dalloc(ctx, &ctx->charge, (size_t)n_ens * ctx->ncell));
     CKI(dalloc(ctx, &ctx->alive, n_ens));
     CKI(dalloc(ctx, &ctx->d_err, 1));
@@ -1290,108 +1356,12 @@ emc_status emc_step(emc_ctx* ctx, int32_t n_steps)
 emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_t dst_is_device, int32_t reset)
 {
     if (!ctx || !dst) return EMC_EINVAL;
-    const int E = ctx->n_ens, C = ctx->ncell;
-    size_t need = 0;
-    switch (kind) {
-    case EMC_TALLY_OBS: need = sizeof(emc_obs) * E; break;
-    case EMC_TALLY_EVENTS: need = 8ull * E * NV * NM; break;
-    case EMC_TALLY_HEAT: need = 8ull * E * C * 2; break;
-    case EMC_TALLY_CHARGE: need = 8ull * E * C; break;
-    case EMC_TALLY_CROSSINGS: need = 8ull * E * 4; break;
-    case EMC_TALLY_PHI: need = 8ull * E * C; break;
-    case EMC_TALLY_FIELD: need = 8ull * E * C * 3; break;
-    case EMC_TALLY_HEAT_J: need = 8ull * E * C; break;
-    default: return fail(ctx, EMC_EINVAL, "unknown tally kind");
-    }
+    const size_t need = tally_bytes(ctx->n_ens, ctx->ncell, kind);
+    if (need == 0) return fail(ctx, EMC_EINVAL, "unknown tally kind");
     if (bytes < need) return fail(ctx, EMC_EINVAL, "destination too small");
     emc_status s = check_err(ctx);
     if (s != EMC_OK) return s;
-    std::vector<unsigned char> host(need);
-    const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
-    if (kind == EMC_TALLY_OBS || kind == EMC_TALLY_CROSSINGS || kind == EMC_TALLY_CHARGE) {
-        std::vector<unsigned long long> cnt((size_t)E * NCNT);
-        std::vector<double> sums((size_t)E * NSUM);
-        CK(cudaMemcpyAsync(cnt.data(), ctx->cnt, 8 * cnt.size(), cudaMemcpyDeviceToHost, ctx->st));
-        CK(cudaMemcpyAsync(sums.data(), ctx->sums, 8 * sums.size(), cudaMemcpyDeviceToHost, ctx->st));
-        std::vector<long long> alive(E, 0);
-        CK(cudaMemcpyAsync(alive.data(), ctx->alive, 8 * E, cudaMemcpyDeviceToHost, ctx->st));
-        std::vector<int> ch;
-        if (kind == EMC_TALLY_CHARGE && nw) {
-            ch.resize((size_t)E * C);
-            CK(cudaMemcpyAsync(ch.data(), ctx->charge, 4 * ch.size(), cudaMemcpyDeviceToHost, ctx->st));
-        }
-        CK(cudaStreamSynchronize(ctx->st));
-        if (kind == EMC_TALLY_OBS) {
-            emc_obs* o = reinterpret_cast<emc_obs*>(host.data());
-            for (int e = 0; e < E; ++e) {
-                const unsigned long long* c = &cnt[(size_t)e * NCNT];
-                const double* sm = &sums[(size_t)e * NSUM];
-                emc_obs& q = o[e];
-                for (int i = 0; i < 3; ++i) q.sum_v[i] = sm[SUM_VX + i] * 1e6;
-                q.sum_E = sm[SUM_E] * kQ;
-                q.sum_Etot = sm[SUM_ETOT] * kQ;
-                q.n_samples = (int64_t)c[CNT_SAMPLES];
-                for (int i = 0; i < 3; ++i) {
-                    q.valley_steps[i] = (int64_t)c[CNT_V0 + i];
-                    q.self_events[i] = (int64_t)c[CNT_SELF0 + i] + (i == 0 ? 0 : 0);
-                }
-                q.overflow = (int64_t)c[CNT_OVERFLOW];
-                q.steps_done = ctx->steps_done;
-                q.n_alive = (int64_t)alive[e];
-                q.inject_starved = (int64_t)c[CNT_STARVED];
-            }
-        } else if (kind == EMC_TALLY_CROSSINGS) {
-            int64_t* o = reinterpret_cast<int64_t*>(host.data());
-            for (int e = 0; e < E; ++e) {
-                o[4 * e + 0] = (int64_t)cnt[(size_t)e * NCNT + CNT_SRC_OUT];
-                o[4 * e + 1] = (int64_t)cnt[(size_t)e * NCNT + CNT_DRN_OUT];
-                o[4 * e + 2] = (int64_t)cnt[(size_t)e * NCNT + CNT_SRC_IN];
-                o[4 * e + 3] = (int64_t)cnt[(size_t)e * NCNT + CNT_DRN_IN];
-            }
-        } else {
-            int64_t* o = reinterpret_cast<int64_t*>(host.data());
-            for (int e = 0; e < E; ++e)
-                for (int c = 0; c < C; ++c) o[(size_t)e * C + c] = nw ? ch[(size_t)e * C + c] : (int64_t)alive[e];
-        }
-    } else if (kind == EMC_TALLY_EVENTS) {
-        CK(cudaMemcpyAsync(host.data(), ctx->events, need, cudaMemcpyDeviceToHost, ctx->st));
-    } else if (kind == EMC_TALLY_HEAT) {
-        CK(cudaMemcpyAsync(host.data(), ctx->heat, need, cudaMemcpyDeviceToHost, ctx->st));
-    } else if (kind == EMC_TALLY_PHI || kind == EMC_TALLY_FIELD) {
-        if (!nw) {
-            std::memset(host.data(), 0, need);
-            if (kind == EMC_TALLY_FIELD) {
-                double* o = reinterpret_cast<double*>(host.data());
-                for (int e = 0; e < E; ++e)
-                    for (int i = 0; i < 3; ++i) o[3 * e + i] = ctx->cfg[e].field_V_m[i];
-            }
-        } else {
-            CK(cudaMemcpyAsync(host.data(), kind == EMC_TALLY_PHI ? ctx->phi : ctx->Efield, need,
-                               cudaMemcpyDeviceToHost, ctx->st));
-        }
-    } else if (kind == EMC_TALLY_HEAT_J) {
-        std::vector<long long> h((size_t)E * C * 2);
-        CK(cudaMemcpyAsync(h.data(), ctx->heat, 8 * h.size(), cudaMemcpyDeviceToHost, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
-        double* o = reinterpret_cast<double*>(host.data());
-        for (int e = 0; e < E; ++e)
-            for (int c = 0; c < C; ++c) {
-                const long long* hc = &h[((size_t)e * C + c) * 2];
-                o[(size_t)e * C + c] =
-                    ((double)hc[0] * ctx->cfg[e].hw_lo_eV + (double)hc[1] * ctx->cfg[e].hw_iv_eV) * kQ * ctx->w[e];
-            }
-    }
-    CK(cudaStreamSynchronize(ctx->st));
-    if (dst_is_device)
-        CK(cudaMemcpyAsync(dst, host.data(), need, cudaMemcpyHostToDevice, ctx->st));
-    else
-        std::memcpy(dst, host.data(), need);
-    if (reset) {
-        CK(cudaMemsetAsync(ctx->events, 0, 8ull * E * NV * NM, ctx->st));
-        CK(cudaMemsetAsync(ctx->cnt, 0, 8ull * E * NCNT, ctx->st));
-        CK(cudaMemsetAsync(ctx->sums, 0, 8ull * E * NSUM, ctx->st));
-        CK(cudaMemsetAsync(ctx->heat, 0, 8ull * E * C * 2, ctx->st));
-    }
+    if ((s = emc_tally_async(ctx, kind, dst, bytes, dst_is_device, reset)) != EMC_OK) return s;
     CK(cudaStreamSynchronize(ctx->st));
     return EMC_OK;
 }
@@ -1405,15 +1375,15 @@ emc_status emc_tally_async(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, 
     if (need == 0) return fail(ctx, EMC_EINVAL, "unknown tally kind");
     if (bytes < need) return fail(ctx, EMC_EINVAL, "destination too small");
     const cudaMemcpyKind dir = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    const void* direct = kind == EMC_TALLY_EVENTS ? (const void*)ctx->events
-                       : kind == EMC_TALLY_HEAT ? (const void*)ctx->heat
+    const void* direct = kind == EMC_TALLY_EVENTS_CELL ? (const void*)ctx->events
+                       : (kind == EMC_TALLY_EVENTS && C == 1) ? (const void*)ctx->events
                        : (nw && kind == EMC_TALLY_PHI) ? (const void*)ctx->phi
                        : (nw && kind == EMC_TALLY_FIELD) ? (const void*)ctx->Efield : nullptr;
     if (direct) {
         CK(cudaMemcpyAsync(dst, direct, need, dir, ctx->st));
     } else {
         if (!ctx->tstage) {
-            CK(dalloc(ctx, &ctx->tstage, tally_bytes(E, C, EMC_TALLY_FIELD) + sizeof(emc_obs) * E));
+            CK(dalloc(ctx, &ctx->tstage, stage_bytes(E, C)));
             CK(dalloc(ctx, &ctx->tpar, (size_t)6 * E));
             std::vector<double> par((size_t)6 * E);
             for (int e = 0; e < E; ++e) {
@@ -1428,18 +1398,18 @@ emc_status emc_tally_async(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, 
         }
         void* out = dst_is_device ? dst : (void*)ctx->tstage;
         const int64_t items = kind == EMC_TALLY_OBS || kind == EMC_TALLY_CROSSINGS ? E
+                            : kind == EMC_TALLY_EVENTS ? (int64_t)E * NV * NM
                             : kind == EMC_TALLY_FIELD ? (int64_t)E * C * 3 : (int64_t)E * C;
         k_tally_pack<<<grid_for(items, 256), 256, 0, ctx->st>>>(kind, E, C, nw ? 1 : 0, ctx->cnt, ctx->sums, ctx->alive,
-                                                                  ctx->charge, ctx->heat, ctx->tpar, ctx->steps_done,
+                                                                  ctx->charge, ctx->events, ctx->tpar, ctx->steps_done,
                                                                   out);
         ctx->launches += 1;
         if (!dst_is_device) CK(cudaMemcpyAsync(dst, ctx->tstage, need, cudaMemcpyDeviceToHost, ctx->st));
     }
     if (reset) {
-        CK(cudaMemsetAsync(ctx->events, 0, 8ull * E * NV * NM, ctx->st));
+        CK(cudaMemsetAsync(ctx->events, 0, 8ull * E * C * NV * NM, ctx->st));
         CK(cudaMemsetAsync(ctx->cnt, 0, 8ull * E * NCNT, ctx->st));
         CK(cudaMemsetAsync(ctx->sums, 0, 8ull * E * NSUM, ctx->st));
-        CK(cudaMemsetAsync(ctx->heat, 0, 8ull * E * C * 2, ctx->st));
     }
     CK(cudaGetLastError());
     return EMC_OK;
@@ -1449,6 +1419,8 @@ emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const doubl
 {
     if (!ctx || !bc_volts) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "poisson_solve needs the nanowire geometry");
+    if (!finite_inputs(charge_or_null, ctx->ncell, bc_volts))
+        return fail(ctx, EMC_EINVAL, "poisson_solve: charge density and voltages must be finite");
     const int n = ctx->ncell;
     double *rho = nullptr, *rhs = nullptr, *phi = nullptr, *bias = nullptr;
     float* r32 = nullptr;
@@ -1517,23 +1489,44 @@ constexpr size_t kStaticDoubles = 3 * (size_t)kStaticCells + 4 + kStaticCells / 
                                   (size_t)kStaticSlices * kStaticCells / 2;
 static __device__ __align__(256) double g_poisson_scratch[kStaticDoubles];
 
-// device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol itself is not a device address)
+// Device address of the scratch array, looked up with cudaGetSymbolAddress
+// once per CUDA context (the host-side symbol itself is not a device
+// address).  The cache is keyed by the context's unique id, so a context
+// created anew after a device reset (which reloads the module) gets its own
+// lookup instead of a stale address.
+typedef CUresult (*ctx_current_fn)(CUcontext*);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long*);
 std::mutex g_scratch_mu;
-void* g_scratch_addr[128] = {nullptr};
+std::map<unsigned long long, void*> g_scratch_addr;
 
 emc_status static_scratch(emc_ctx* ctx, double** out)
 {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) return fail(ctx, EMC_EINVAL, "device ordinal out of range for the static scratch");
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    static ctx_current_fn get_current = nullptr;
+    static ctx_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        CK(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&get_current), 12000,
+                                            cudaEnableDefault, &q1));
+        CK(cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&get_id), 12000,
+                                            cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+            get_current = nullptr;
+            get_id = nullptr;
+            return fail(ctx, EMC_ECUDA, "static scratch: driver context queries unavailable");
+        }
+    }
+    CUcontext cu = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&cu) != CUDA_SUCCESS || !cu || get_id(cu, &id) != CUDA_SUCCESS)
+        return fail(ctx, EMC_ESTATE, "static scratch: no current CUDA context on this thread");
+    auto it = g_scratch_addr.find(id);
+    if (it == g_scratch_addr.end()) {
         void* p = nullptr;
         CK(cudaGetSymbolAddress(&p, g_poisson_scratch));
-        g_scratch_addr[dev] = p;
+        it = g_scratch_addr.emplace(id, p).first;
     }
-    *out = static_cast<double*>(g_scratch_addr[dev]);
+    *out = static_cast<double*>(it->second);
     return EMC_OK;
 }
 }  // namespace
@@ -1546,6 +1539,8 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, 
     if (!ctx || !bc_volts) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE)
         return fail(ctx, EMC_ESTATE, "emc_poisson_solve_static needs the nanowire geometry");
+    if (!finite_inputs(charge_or_null, ctx->ncell, bc_volts))
+        return fail(ctx, EMC_EINVAL, "emc_poisson_solve_static: charge density and voltages must be finite");
     const int n = ctx->ncell;
     if (n > kStaticCells) {
         char buf[160];
@@ -1575,11 +1570,12 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, 
         k_rhs<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, ctx->charge, nullptr, ctx->d_w, ctx->d_Nd, Vcell,
                                                      kE2Eps0 / ctx->cfg[0].eps_s, bias, rhs);
     }
-    for (int sw = 0; sw < kPoissonSweeps + 2; ++sw) {
+    // the same sweeps as poisson_solve, so the two give the same potential
+    for (int sw = 0; sw < kPoissonSweeps + 1; ++sw) {
         k_resid<<<grid_for(n, 256), 256, 0, ctx->st>>>(G, 1, rhs, phi, r32);
         launch_sweep(ctx->G32, r32, part, phi, n, 1, ctx->st);
     }
-    ctx->launches += 1 + 3 * (kPoissonSweeps + 2);
+    ctx->launches += 1 + 3 * (kPoissonSweeps + 1);
     CK(cudaGetLastError());
     if (phi_out_or_null)
         CK(cudaMemcpyAsync(phi_out_or_null, phi, 8 * (size_t)n, cudaMemcpyDeviceToHost, ctx->st));
@@ -1587,9 +1583,154 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, 
     return EMC_OK;
 }
 
+// ------------------------------------------------------- checkpoint/resume
+// The blob: StateHeader, then the sections of state_sections() in order.
+namespace {
+constexpr uint64_t kStateMagic = 0x4554415453434d45ull;  // "EMCSTATE"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+    uint64_t magic;
+    uint32_t version, precision, geometry, tmode;
+    int32_t n_ens, ncell;
+    int64_t n_slots, bits_words, steps_done, flights_since_sort;
+    uint64_t cfg_hash;
+};
+static_assert(sizeof(StateHeader) == 72, "the state header layout is part of the ABI");
+
+// FNV-1a over the configurations, launch-tuning fields zeroed: a state can
+// only be restored into a context made from the same ensembles
+uint64_t cfg_hash(const emc_ctx* ctx)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (emc_config c : ctx->cfg) {
+        c.sort_period = c.block_size = c.steps_per_launch = c.table_smem_kb = 0;
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&c);
+        for (size_t i = 0; i < sizeof c; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+    return h;
+}
+
+struct Section {
+    void* p;        // device buffer, or host memory when host = true
+    size_t bytes;
+    bool host;
+};
+
+std::vector<Section> state_sections(emc_ctx* ctx, bool tmode)
+{
+    const size_t n = (size_t)ctx->n_slots, E = ctx->n_ens, C = ctx->ncell;
+    const size_t es = ctx->prec == EMC_FP64 ? 8 : 4;
+    const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
+    std::vector<Section> v = {{ctx->kx, es * n, false}, {ctx->ky, es * n, false}, {ctx->kz, es * n, false}};
+    if (nw) v.insert(v.end(), {{ctx->x, es * n, false}, {ctx->y, es * n, false}, {ctx->z, es * n, false}});
+    v.insert(v.end(), {{ctx->tr, es * n, false}, {ctx->tag, 4 * n, false}, {ctx->ctr, 8 * n, false},
+                       {ctx->id, 4 * n, false}, {ctx->slot_of_id, 4 * n, false},
+                       {ctx->dead_bits, 4 * (size_t)ctx->bits_words, false},
+                       {ctx->events, 8 * E * C * NV * NM, false}, {ctx->cnt, 8 * E * NCNT, false},
+                       {ctx->sums, 8 * E * NSUM, false}, {ctx->charge, 4 * E * C, false}, {ctx->alive, 8 * E, false},
+                       {ctx->d_err, 4, false}, {ctx->bias.data(), 8 * 3 * E, true}});
+    if (nw)
+        v.insert(v.end(), {{ctx->d_bias, 8 * 3 * E, false}, {ctx->phi, 8 * E * C, false},
+                           {ctx->Efield, 24 * E * C, false}, {ctx->acc_cell, 4 * es * E * C, false}});
+    if (tmode)
+        v.insert(v.end(), {{ctx->cell_bin, 4 * E * C, false}, {ctx->ens_g0, es * E * NV, false},
+                           {ctx->ens_ig0, es * E * NV, false}, {ctx->ens_g0_host.data(), 8 * E * NV, true},
+                           {ctx->cell_bin_host.data(), 4 * E * C, true}});
+    return v;
+}
+
+size_t state_bytes(emc_ctx* ctx, bool tmode)
+{
+    size_t b = sizeof(StateHeader);
+    for (const Section& s : state_sections(ctx, tmode)) b += s.bytes;
+    return b;
+}
+}  // namespace
+
+emc_status emc_state_size(emc_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return EMC_EINVAL;
+    *bytes = state_bytes(ctx, ctx->cell_bin != nullptr);
+    return EMC_OK;
+}
+
+emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes)
+{
+    if (!ctx || !dst) return EMC_EINVAL;
+    const bool tmode = ctx->cell_bin != nullptr;
+    if (bytes < state_bytes(ctx, tmode)) return fail(ctx, EMC_EINVAL, "emc_get_state: destination too small");
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.version = kStateVersion;
+    h.precision = (uint32_t)ctx->prec;
+    h.geometry = (uint32_t)ctx->geom;
+    h.tmode = tmode ? 1u : 0u;
+    h.n_ens = ctx->n_ens;
+    h.ncell = ctx->ncell;
+    h.n_slots = ctx->n_slots;
+    h.bits_words = ctx->bits_words;
+    h.steps_done = ctx->steps_done;
+    h.flights_since_sort = ctx->flights_since_sort;
+    h.cfg_hash = cfg_hash(ctx);
+    unsigned char* out = static_cast<unsigned char*>(dst);
+    std::memcpy(out, &h, sizeof h);
+    size_t off = sizeof h;
+    for (const Section& s : state_sections(ctx, tmode)) {
+        if (s.host) std::memcpy(out + off, s.p, s.bytes);
+        else if (s.bytes) CK(cudaMemcpyAsync(out + off, s.p, s.bytes, cudaMemcpyDeviceToHost, ctx->st));
+        off += s.bytes;
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
+emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes)
+{
+    if (!ctx || !src) return EMC_EINVAL;
+    if (bytes < sizeof(StateHeader)) return fail(ctx, EMC_EINVAL, "emc_set_state: blob too small");
+    StateHeader h;
+    std::memcpy(&h, src, sizeof h);
+    if (h.magic != kStateMagic || h.version != kStateVersion)
+        return fail(ctx, EMC_EINVAL, "emc_set_state: not a state blob of this library version");
+    if (h.precision != (uint32_t)ctx->prec || h.geometry != (uint32_t)ctx->geom || h.n_ens != ctx->n_ens ||
+        h.ncell != ctx->ncell || h.n_slots != ctx->n_slots || h.bits_words != ctx->bits_words ||
+        h.cfg_hash != cfg_hash(ctx))
+        return fail(ctx, EMC_ESTATE, "emc_set_state: the blob belongs to a context of other ensembles");
+    const bool tmode = h.tmode != 0;
+    if (!tmode && ctx->cell_bin)
+        return fail(ctx, EMC_ESTATE, "emc_set_state: this context has subcell temperatures, the blob has none");
+    if (bytes < state_bytes(ctx, tmode)) return fail(ctx, EMC_EINVAL, "emc_set_state: blob too small");
+    if (tmode && !ctx->cell_bin) {
+        emc_status s = ctx->prec == EMC_FP64 ? build_bins<double>(ctx) : build_bins<float>(ctx);
+        if (s != EMC_OK) return s;
+        fill_params(ctx);
+        if (ctx->g_tail_exec) {  // the captured tail holds the kernel parameters
+            CK(cudaGraphExecDestroy(ctx->g_tail_exec));
+            CK(cudaGraphDestroy(ctx->g_tail));
+            ctx->g_tail_exec = nullptr;
+            ctx->g_tail = nullptr;
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    const unsigned char* in = static_cast<const unsigned char*>(src);
+    size_t off = sizeof h;
+    for (const Section& s : state_sections(ctx, tmode)) {
+        if (s.host) std::memcpy(s.p, in + off, s.bytes);
+        else if (s.bytes) CK(cudaMemcpyAsync(s.p, in + off, s.bytes, cudaMemcpyHostToDevice, ctx->st));
+        off += s.bytes;
+    }
+    ctx->steps_done = h.steps_done;
+    ctx->flights_since_sort = h.flights_since_sort;
+    CK(cudaStreamSynchronize(ctx->st));
+    return EMC_OK;
+}
+
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg)
 {
     if (!ctx || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
+    if (!std::isfinite(Vs) || !std::isfinite(Vd) || !std::isfinite(Vg))
+        return fail(ctx, EMC_EINVAL, "emc_set_bias: terminal voltages must be finite");
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias needs the nanowire geometry");
     const bool same = ctx->bias[3 * ens] == Vs && ctx->bias[3 * ens + 1] == Vd && ctx->bias[3 * ens + 2] == Vg;
     ctx->bias[3 * ens] = Vs;
@@ -1609,12 +1750,50 @@ emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias)
 {
     if (!ctx || !bias) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias_all needs the nanowire geometry");
+    for (int i = 0; i < 3 * ctx->n_ens; ++i)
+        if (!std::isfinite(bias[i])) return fail(ctx, EMC_EINVAL, "emc_set_bias_all: terminal voltages must be finite");
     const bool same = std::memcmp(ctx->bias.data(), bias, sizeof(double) * 3 * ctx->n_ens) == 0;
     std::memcpy(ctx->bias.data(), bias, sizeof(double) * 3 * ctx->n_ens);
     CK(cudaMemcpyAsync(ctx->d_bias, bias, sizeof(double) * 3 * ctx->n_ens, cudaMemcpyHostToDevice, ctx->st));
     // the field already belongs to these terminal voltages when none changed
     if (same) return EMC_OK;
     return ctx->prec == EMC_FP64 ? poisson_update<double>(ctx) : poisson_update<float>(ctx);
+}
+
+emc_status emc_surrogate_train(emc_ctx* ctx, const emc_mlp_config* net, const float* X, const float* Y, int64_t n,
+                               const emc_train_config* tc, float* loss_history)
+{
+    if (!ctx || !net || !X || !Y || !tc) return EMC_EINVAL;
+    if (ctx->sur) {
+        emc_mlp_destroy(ctx->sur);
+        ctx->sur = nullptr;
+    }
+    emc_mlp* m = nullptr;
+    emc_status s = emc_mlp_create(net, ctx->st, &m);
+    if (s == EMC_OK) s = emc_mlp_train(m, X, Y, n, tc, loss_history);
+    if (s != EMC_OK) {
+        const std::string msg = m ? emc_mlp_last_error(m) : "surrogate network";
+        if (m) emc_mlp_destroy(m);
+        return fail(ctx, s, "emc_surrogate_train: " + msg);
+    }
+    ctx->sur = m;
+    return EMC_OK;
+}
+
+emc_status emc_surrogate_infer(emc_ctx* ctx, const float* X, float* Y, int64_t n)
+{
+    if (!ctx || n < 0 || (n > 0 && (!X || !Y))) return EMC_EINVAL;
+    if (!ctx->sur) return fail(ctx, EMC_ESTATE, "emc_surrogate_infer: no surrogate trained on this context");
+    const emc_status s = emc_mlp_infer(ctx->sur, X, Y, n);
+    if (s != EMC_OK) return fail(ctx, s, std::string("emc_surrogate_infer: ") + emc_mlp_last_error(ctx->sur));
+    return EMC_OK;
+}
+
+emc_status emc_surrogate_params(emc_ctx* ctx, float* dst, int64_t* count)
+{
+    if (!ctx || !count) return EMC_EINVAL;
+    if (!ctx->sur) return fail(ctx, EMC_ESTATE, "emc_surrogate_params: no surrogate trained on this context");
+    return emc_mlp_params(ctx->sur, dst, nullptr, count);
 }
 
 emc_status emc_profile(emc_ctx* ctx, int32_t enable)
@@ -1742,6 +1921,7 @@ void emc_destroy(emc_ctx* ctx)
     cudaStreamSynchronize(ctx->st);
     if (ctx->g_tail_exec) cudaGraphExecDestroy(ctx->g_tail_exec);
     if (ctx->g_tail) cudaGraphDestroy(ctx->g_tail);
+    if (ctx->sur) emc_mlp_destroy(ctx->sur);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;

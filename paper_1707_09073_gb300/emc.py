@@ -20,6 +20,7 @@ GEOM_BULK, GEOM_NANOWIRE = 0, 1
 FP32, FP64 = 0, 1
 TALLY_OBS, TALLY_EVENTS, TALLY_HEAT, TALLY_CHARGE = 0, 1, 2, 3
 TALLY_CROSSINGS, TALLY_PHI, TALLY_FIELD, TALLY_HEAT_J = 4, 5, 6, 7
+TALLY_EVENTS_CELL = 8
 STATUS = {0: "EMC_OK", 1: "EMC_EINVAL", 2: "EMC_ENOMEM", 3: "EMC_ECUDA", 4: "EMC_EOVERFLOW",
           5: "EMC_ETIMEOUT", 6: "EMC_ESTATE"}
 
@@ -81,6 +82,9 @@ def lib():
         L.emc_set_bias.argtypes = [P, I32, C.c_double, C.c_double, C.c_double]
         L.emc_set_bias_all.argtypes = [P, dp]
         L.emc_set_temperature.argtypes = [P, I32, dp, I32]
+        L.emc_state_size.argtypes = [P, C.POINTER(C.c_size_t)]
+        L.emc_get_state.argtypes = [P, P, C.c_size_t]
+        L.emc_set_state.argtypes = [P, P, C.c_size_t]
         L.emc_profile.argtypes = [P, I32]
         L.emc_profile_read.argtypes = [P, dp, C.POINTER(I64)]
         L.emc_debug_philox.argtypes = [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32), I32]
@@ -96,7 +100,8 @@ def lib():
         for f in ("emc_init", "emc_batch_init", "emc_step", "emc_tally", "emc_tally_async", "poisson_solve",
                   "emc_poisson_solve_static", "emc_set_bias",
                   "emc_set_bias_all", "emc_set_temperature", "emc_profile", "emc_profile_read",
-                  "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape"):
+                  "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape",
+                  "emc_state_size", "emc_get_state", "emc_set_state"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -191,6 +196,7 @@ class Context:
             TALLY_PHI: (np.dtype(np.float64), (E, Cc)),
             TALLY_FIELD: (np.dtype(np.float64), (E, Cc, 3)),
             TALLY_HEAT_J: (np.dtype(np.float64), (E, Cc)),
+            TALLY_EVENTS_CELL: (np.dtype(np.uint64), (E, Cc, NV, NM)),
         }[kind]
 
     def pinned_tally(self, kind: int) -> np.ndarray:
@@ -237,6 +243,7 @@ class Context:
             TALLY_PHI: (np.float64, (E, Cc)),
             TALLY_FIELD: (np.float64, (E, Cc, 3)),
             TALLY_HEAT_J: (np.float64, (E, Cc)),
+            TALLY_EVENTS_CELL: (np.uint64, (E, Cc, NV, NM)),
         }[kind]
         if device:
             nbytes = C.sizeof(spec[0]) if kind == TALLY_OBS else int(np.prod(spec[1])) * np.dtype(spec[0]).itemsize
@@ -288,6 +295,48 @@ class Context:
         """Lattice temperature (K) of every subcell of ensemble `ens`."""
         T = np.ascontiguousarray(np.atleast_1d(T_cells), dtype=np.float64)
         self._check(lib().emc_set_temperature(self.h, int(ens), _p(T), int(T.size)))
+
+    def emc_get_state(self) -> np.ndarray:
+        """The whole simulation state as a byte array (emc_get_state)."""
+        n = C.c_size_t()
+        self._check(lib().emc_state_size(self.h, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.uint8)
+        self._check(lib().emc_get_state(self.h, out.ctypes.data_as(C.c_void_p), out.nbytes))
+        return out
+
+    def emc_set_state(self, blob):
+        """Restore a state from emc_get_state of a context of the same ensembles."""
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        self._check(lib().emc_set_state(self.h, b.ctypes.data_as(C.c_void_p), b.nbytes))
+
+    def emc_surrogate_train(self, net: "EmcMlpConfig", X, Y, steps, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
+                            eps=1e-8, seed=0):
+        """Create and train the context's surrogate (emc_surrogate_train);
+        returns the loss history."""
+        L = _surrogate_lib()
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        t = train_config(steps, batch, lr, beta1, beta2, eps, seed)
+        hist = np.zeros(max(steps, 1), dtype=np.float32)
+        self._check(L.emc_surrogate_train(self.h, C.byref(net), _p(X, C.c_float), _p(Y, C.c_float), X.shape[0],
+                                          C.byref(t), _p(hist, C.c_float)))
+        self._sur_out = net.n_out
+        return hist[:steps]
+
+    def emc_surrogate_infer(self, X):
+        L = _surrogate_lib()
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], getattr(self, "_sur_out", 16)), dtype=np.float32)
+        self._check(L.emc_surrogate_infer(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0]))
+        return Y
+
+    def emc_surrogate_params(self):
+        L = _surrogate_lib()
+        n = C.c_int64()
+        self._check(L.emc_surrogate_params(self.h, None, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.float32)
+        self._check(L.emc_surrogate_params(self.h, _p(out, C.c_float), C.byref(n)))
+        return out
 
     def emc_profile(self, enable: bool):
         self._check(lib().emc_profile(self.h, int(enable)))
@@ -425,20 +474,46 @@ def _mlp_lib():
     return L
 
 
+def mlp_config(n_in, n_hidden, n_layers, n_out, x_shift, x_scale, y_shift, y_scale, seed=0) -> EmcMlpConfig:
+    """The emc_mlp_config struct (unused normalisation slots: shift 0, scale 1)."""
+    c = EmcMlpConfig()
+    c.n_in, c.n_hidden, c.n_layers, c.n_out, c.seed = n_in, n_hidden, n_layers, n_out, seed
+    for arr, vals in ((c.x_shift, x_shift), (c.x_scale, x_scale), (c.y_shift, y_shift), (c.y_scale, y_scale)):
+        for i, v in enumerate(vals):
+            arr[i] = float(v)
+    for i in range(n_in, 16):
+        c.x_scale[i] = 1.0
+    for i in range(n_out, 16):
+        c.y_scale[i] = 1.0
+    return c
+
+
+def train_config(steps, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> EmcTrainConfig:
+    t = EmcTrainConfig()
+    t.steps, t.batch, t.lr, t.beta1, t.beta2, t.eps, t.seed = steps, batch, lr, beta1, beta2, eps, seed
+    return t
+
+
+def _surrogate_lib():
+    L = _mlp_lib()
+    if not getattr(L, "_sur_ready", False):
+        P, I64 = C.c_void_p, C.c_int64
+        fp = C.POINTER(C.c_float)
+        L.emc_surrogate_train.argtypes = [P, C.POINTER(EmcMlpConfig), fp, fp, I64, C.POINTER(EmcTrainConfig), fp]
+        L.emc_surrogate_infer.argtypes = [P, fp, fp, I64]
+        L.emc_surrogate_params.argtypes = [P, fp, C.POINTER(I64)]
+        for f in ("emc_surrogate_train", "emc_surrogate_infer", "emc_surrogate_params"):
+            getattr(L, f).restype = C.c_int
+        L._sur_ready = True
+    return L
+
+
 class Mlp:
     """The surrogate network of the C ABI (emc_mlp_*).  x_shift/x_scale and
     y_shift/y_scale normalise inputs and outputs inside the library."""
 
     def __init__(self, n_in, n_hidden, n_layers, n_out, x_shift, x_scale, y_shift, y_scale, seed=0, stream=None):
-        c = EmcMlpConfig()
-        c.n_in, c.n_hidden, c.n_layers, c.n_out, c.seed = n_in, n_hidden, n_layers, n_out, seed
-        for arr, vals in ((c.x_shift, x_shift), (c.x_scale, x_scale), (c.y_shift, y_shift), (c.y_scale, y_scale)):
-            for i, v in enumerate(vals):
-                arr[i] = float(v)
-        for i in range(n_in, 16):
-            c.x_scale[i] = 1.0
-        for i in range(n_out, 16):
-            c.y_scale[i] = 1.0
+        c = mlp_config(n_in, n_hidden, n_layers, n_out, x_shift, x_scale, y_shift, y_scale, seed)
         self.cfg = c
         self.n_in, self.n_out = n_in, n_out
         self.h = C.c_void_p()
@@ -463,8 +538,7 @@ class Mlp:
     def train(self, X, Y, steps, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0):
         X = np.ascontiguousarray(X, dtype=np.float32)
         Y = np.ascontiguousarray(Y, dtype=np.float32)
-        t = EmcTrainConfig()
-        t.steps, t.batch, t.lr, t.beta1, t.beta2, t.eps, t.seed = steps, batch, lr, beta1, beta2, eps, seed
+        t = train_config(steps, batch, lr, beta1, beta2, eps, seed)
         hist = np.zeros(max(steps, 1), dtype=np.float32)
         self._check(_mlp_lib().emc_mlp_train(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0], C.byref(t),
                                              _p(hist, C.c_float)))

@@ -90,3 +90,58 @@ def test_full_size_inference_sampled(emc):
     idx = rng.choice(X.shape[0], 3000, replace=False)
     want = ref.predict(net.params().astype(np.float64), sizes, X[idx], nrm)
     assert np.abs(got[idx] - want).max() / np.abs(want - nrm["y_shift"]).max() < 3e-2
+
+
+@pytest.mark.parametrize("hidden,layers,rows", [(128, 3, 512), (48, 2, 1000)])
+def test_gradient_per_tensor_elementwise(emc, hidden, layers, rows):
+    """Every element of every parameter tensor (W and b of each layer) of the
+    tensor-core gradient against the FP64 reference.  BF16 operands round to
+    u = 2^-9 relative; an element's operands come out of the forward chain
+    (activations) and the backward chain (deltas), each up to `depth` rounded
+    products deep, two roundings per product, so it may err by
+    2 x 2 depth x u x the sum of the absolute values of its products (from
+    the FP64 reference).  The per-tensor relative error and direction are
+    checked too."""
+    net, nrm, sizes, rng = make(emc, hidden=hidden, layers=layers, seed=17)
+    X = rng.normal(size=(rows, 4)).astype(np.float32)
+    Y = rng.normal(size=(rows, 7)).astype(np.float32)
+    _, g = net.grad(X, Y)
+    theta = net.params().astype(np.float64)
+    _, gref = ref.loss_and_grad(theta, sizes, X, Y, nrm)
+    S = ref.grad_abs_products(theta, sizes, X, Y, nrm)
+    depth = len(sizes) - 1
+    tol = 4.0 * depth * 2.0 ** -9 * S + 1e-7 * np.abs(gref).max()
+    off = 0
+    for l, (a, b) in enumerate(zip(sizes[:-1], sizes[1:])):
+        for name, cnt in (("W", a * b), ("b", b)):
+            sl = slice(off, off + cnt)
+            off += cnt
+            err = np.abs(g[sl] - gref[sl])
+            assert (err <= tol[sl]).all(), (l, name, float((err / tol[sl]).max()))
+            rel = np.linalg.norm(g[sl] - gref[sl]) / np.linalg.norm(gref[sl])
+            cos = float(g[sl] @ gref[sl] / (np.linalg.norm(g[sl]) * np.linalg.norm(gref[sl])))
+            assert rel < 0.03 and cos > 0.999, (l, name, rel, cos)
+    assert off == g.size
+
+
+def test_surrogate_on_the_context_equals_the_standalone_network(emc):
+    """emc_surrogate_train / emc_surrogate_infer on a Monte Carlo context run
+    the same kernels as the standalone network: the same training gives the
+    same loss history and predictions (to the rounding order of the split-K
+    FP32 atomic sums, which may differ between runs)."""
+    import workloads as W
+    rng = np.random.default_rng(21)
+    X = rng.uniform(-1, 1, size=(4000, 4)).astype(np.float32)
+    Y = np.stack([X[:, 0] * X[:, 1], np.sin(X[:, 2]), X[:, 3] ** 2], axis=1).astype(np.float32)
+    args = (4, 64, 2, 3, np.zeros(4), np.ones(4), np.zeros(3), np.ones(3))
+    net = emc.emc.Mlp(*args, seed=4)
+    h1 = net.train(X, Y, steps=200, batch=256, lr=2e-3, seed=8)
+    with emc.Context(W.bulk(n_particles=10)) as ctx:
+        with pytest.raises(emc.EmcError):
+            ctx.emc_surrogate_infer(X[:5])
+        h2 = ctx.emc_surrogate_train(emc.emc.mlp_config(*args, seed=4), X, Y, steps=200, batch=256, lr=2e-3, seed=8)
+        np.testing.assert_allclose(h2, h1, rtol=1e-2)
+        p1, p2 = net.params(), ctx.emc_surrogate_params()
+        assert p1.size == p2.size and np.linalg.norm(p2 - p1) <= 1e-3 * np.linalg.norm(p1)
+        y1, y2 = net.infer(X[:300]), ctx.emc_surrogate_infer(X[:300])
+        assert y2.shape == y1.shape and np.abs(y2 - y1).max() <= 1e-2 * np.abs(y1).max()

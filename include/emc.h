@@ -101,7 +101,7 @@ typedef struct emc_config {
     int32_t precision;      /* EMC_FP32 (production) or EMC_FP64 (parity build) */
     int32_t sort_period;    /* sort particles every this many launches (0 = never) */
     int32_t block_size;     /* flight-kernel threads per block (0 = default 256) */
-    int32_t steps_per_launch; /* bulk: steps fused per flight launch (0 = default 50) */
+    int32_t steps_per_launch; /* bulk: steps fused per flight launch (0 = default 50, at most 1000) */
     int32_t table_smem_kb;  /* rate-table bytes staged in shared memory per block, KiB
                                (0 = default 32; bins above it are read through L1/L2) */
 } emc_config;

@@ -133,5 +133,17 @@ __host__ __device__ __forceinline__ Real u01(uint32_t x)
 {
     return Real(2u * (x >> 9) + 1u) * Real(5.9604644775390625e-08);
 }
+// The same number without an integer-to-float conversion: the top 23 bits
+// as the mantissa of a float in [1, 2), minus 1 (exact), plus 2^-24 (exact:
+// the sum has 24 significant bits).
+template <>
+__host__ __device__ __forceinline__ float u01<float>(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-08f;
+#else
+    return float(2u * (x >> 9) + 1u) * 5.9604644775390625e-08f;
+#endif
+}
 
 }  // namespace emc

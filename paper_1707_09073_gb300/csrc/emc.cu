@@ -563,6 +563,8 @@ emc_status validate(const emc_config* c, int n, emc_ctx* ctx)
         if (b.block_size != 0 && (b.block_size < 32 || b.block_size > 256 || b.block_size % 32))
             return fail(ctx, EMC_EINVAL, "block_size: multiple of 32 in [32, 256]");
         if (b.table_smem_kb < 0 || b.table_smem_kb > 200) return fail(ctx, EMC_EINVAL, "table_smem_kb in [0, 200]");
+        if (b.steps_per_launch > 1000 || b.steps_per_poisson > 1000)
+            return fail(ctx, EMC_EINVAL, "steps_per_launch and steps_per_poisson at most 1000");
     }
     return EMC_OK;
 }

@@ -44,6 +44,8 @@ struct Mth<float> {
     }
     static __device__ __forceinline__ float cospi_(float x) { return cospif(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+    static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
 };
 template <>
 struct Mth<double> {
@@ -55,14 +57,29 @@ struct Mth<double> {
     static __device__ __forceinline__ void sincos2pi_u(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
     static __device__ __forceinline__ double cospi_(double x) { return cospi(x); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+    static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ double copysign_(double a, double b) { return copysign(a, b); }
 };
+
+// Fused multiply-add, written out so that every kernel that inlines the
+// particle arithmetic rounds it the same way (the compiler may otherwise fuse
+// a*b + c*d either way round, differently in different kernels).
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Kinetic energy whose Kane gamma is g: the positive root of E(1 + aE) = g,
 // written as 2g / (1 + sqrt(1 + 4ag)) (exact for a = 0, no cancellation).
 template <typename Real>
 __device__ __forceinline__ Real kane_E(Real g, Real a)
 {
-    return Real(2) * g / (Real(1) + Mth<Real>::sqrt_(Real(1) + Real(4) * a * g));
+    return Real(2) * g / (Real(1) + Mth<Real>::sqrt_(fma_(Real(4) * a, g, Real(1))));
+}
+
+// |k|^2
+template <typename Real>
+__device__ __forceinline__ Real norm2(Real x, Real y, Real z)
+{
+    return fma_(z, z, fma_(y, y, x * x));
 }
 
 // Compensated (Kahan) accumulator for the float build; plain sum for double.
@@ -205,7 +222,7 @@ __device__ void new_electron(Part<Real>& q, const Phys<Real>* ph, const Real lo[
     Real km = Mth<Real>::sqrt_(E * (Real(1) + ph->alpha[0] * E) / ph->ck[0]);
     U4 r = q.draw();
     Real ct = Real(1) - Real(2) * u01<Real>(r.a);
-    Real st = Mth<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
+    Real st = Mth<Real>::sqrt_(Mth<Real>::max_(Real(0), fma_(-ct, ct, Real(1))));
     Real sp, cp;
     Mth<Real>::sincospi_(Real(2) * u01<Real>(r.b), &sp, &cp);
     q.kx = km * st * cp;
@@ -246,29 +263,29 @@ template <typename Real, bool NW>
 __device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>& ph, const Real f4[4], Real t)
 {
     const Real k0x = q.kx, k0y = q.ky, k0z = q.kz;
-    q.kx = k0x + f4[0] * t;
-    q.ky = k0y + f4[1] * t;
-    q.kz = k0z + f4[2] * t;
+    q.kx = fma_(f4[0], t, k0x);
+    q.ky = fma_(f4[1], t, k0y);
+    q.kz = fma_(f4[2], t, k0z);
     const int v = q.v;
     const Real al = ph.alpha[v];
     const Real E0 = q.E;
-    const Real E1 = kane_E(ph.ck[v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), al);
+    const Real E1 = kane_E(ph.ck[v] * norm2(q.kx, q.ky, q.kz), al);
     q.E = E1;
-    const Real f1 = ph.vk[v] / (Real(1) + Real(2) * al * E1);
+    const Real f1 = ph.vk[v] / fma_(Real(2) * al, E1, Real(1));
     if (NW) {
         const Real f0 = q.f;
         const Real h = Real(0.5) * t;
-        Real dx = h * (f0 * k0x + f1 * q.kx);
-        Real dy = h * (f0 * k0y + f1 * q.ky);
-        Real dz = h * (f0 * k0z + f1 * q.kz);
+        Real dx = h * fma_(f0, k0x, f1 * q.kx);
+        Real dy = h * fma_(f0, k0y, f1 * q.ky);
+        Real dz = h * fma_(f0, k0z, f1 * q.kz);
         const Real ihF = f4[3];
         if (ihF > Real(0)) {
             const Real s = Real(kHbarEVfs) * ihF;  // 1/|a|
             const Real ax = f4[0] * s, ay = f4[1] * s, az = f4[2] * s;
-            const Real d = (E1 - E0) * ihF - (dx * ax + dy * ay + dz * az);
-            dx += d * ax;
-            dy += d * ay;
-            dz += d * az;
+            const Real d = fma_(E1 - E0, ihF, -fma_(dz, az, fma_(dy, ay, dx * ax)));
+            dx = fma_(d, ax, dx);
+            dy = fma_(d, ay, dy);
+            dz = fma_(d, az, dz);
         }
         q.x += dx;
         q.y += dy;
@@ -285,7 +302,7 @@ __device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>& ph, const
 template <typename Real>
 __device__ __forceinline__ void diffuse(Part<Real>& q, int axis, Real sn, U4 r)
 {
-    const Real km = Mth<Real>::sqrt_(q.kx * q.kx + q.ky * q.ky + q.kz * q.kz);
+    const Real km = Mth<Real>::sqrt_(norm2(q.kx, q.ky, q.kz));
     const Real u1 = u01<Real>(r.b);
     const Real ca = Mth<Real>::sqrt_(u1), sa = Mth<Real>::sqrt_(Real(1) - u1);
     Real sp, cp;
@@ -451,9 +468,9 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
         j = (mech - 4) >> 1;
         Ep = E + ((mech & 1) == 0 ? ph.hw_iv : -ph.hw_iv) - (ph.Ec[j] - ph.Ec[v]);
     }
-    const Real k2 = q.kx * q.kx + q.ky * q.ky + q.kz * q.kz;
+    const Real k2 = norm2(q.kx, q.ky, q.kz);
     const Real km = Mth<Real>::sqrt_(k2);
-    const Real kp = Mth<Real>::sqrt_(Ep * (Real(1) + ph.alpha[j] * Ep) / ph.ck[j]);
+    const Real kp = Mth<Real>::sqrt_(Ep * fma_(ph.alpha[j], Ep, Real(1)) / ph.ck[j]);
     Real ct;
     bool rel = true;
     if (mech == 0) {
@@ -471,7 +488,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
     }
     Real sp, cp;
     Mth<Real>::sincos2pi_u(u01<Real>(Q.r3), &sp, &cp);
-    const Real st = Mth<Real>::sqrt_(fmax(Real(0), Real(1) - ct * ct));
+    const Real st = Mth<Real>::sqrt_(Mth<Real>::max_(Real(0), fma_(-ct, ct, Real(1))));
     Real dx, dy, dz;
     if (rel) {
         // frame of k: branchless orthonormal basis (Duff et al., JCGT 2017)
@@ -482,15 +499,15 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
             ny = q.ky * ik;
             nz = q.kz * ik;
         }
-        const Real sg = copysign(Real(1), nz);
+        const Real sg = Mth<Real>::copysign_(Real(1), nz);
         const Real aa = Real(-1) / (sg + nz);
         const Real bb = nx * ny * aa;
-        const Real e1x = Real(1) + sg * nx * nx * aa, e1y = sg * bb, e1z = -sg * nx;
-        const Real e2x = bb, e2y = sg + ny * ny * aa, e2z = -ny;
+        const Real e1x = fma_(sg * nx * nx, aa, Real(1)), e1y = sg * bb, e1z = -sg * nx;
+        const Real e2x = bb, e2y = fma_(ny * ny, aa, sg), e2z = -ny;
         const Real sc = st * cp, ss = st * sp;
-        dx = sc * e1x + ss * e2x + ct * nx;
-        dy = sc * e1y + ss * e2y + ct * ny;
-        dz = sc * e1z + ss * e2z + ct * nz;
+        dx = fma_(ct, nx, fma_(ss, e2x, sc * e1x));
+        dy = fma_(ct, ny, fma_(ss, e2y, sc * e1y));
+        dz = fma_(ct, nz, fma_(ss, e2z, sc * e1z));
     } else {
         dx = st * cp;
         dy = st * sp;
@@ -500,7 +517,7 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
     q.ky = kp * dy;
     q.kz = kp * dz;
     q.E = Ep;
-    q.f = ph.vk[j] / (Real(1) + Real(2) * ph.alpha[j] * Ep);
+    q.f = ph.vk[j] / fma_(Real(2) * ph.alpha[j], Ep, Real(1));
     if (NW) {
         // real events per (subcell, valley, mechanism): the subcell heat map
         // (net phonon emission) and the mechanism statistics both follow
@@ -534,42 +551,48 @@ __device__ __forceinline__ Real warp_sum(Real x)
 template <typename Real>
 struct Samples {
     Acc<Real> v[3], E, Et;
-    unsigned int nv[NV] = {0u, 0u, 0u};
+    // particle-steps per valley, 21 bits each (a lane flushes long before
+    // 2^21 of them: at every change of ensemble and at the end of a launch)
+    unsigned long long nv = 0ull;
     int e = -1;
 
+    __device__ __forceinline__ void count_valley(int vv) { nv += 1ull << (21 * vv); }
+    __device__ __forceinline__ unsigned int nvalley(int vv) const { return unsigned((nv >> (21 * vv)) & 0x1FFFFFull); }
+
     // Called by all 32 lanes of the warp; lanes with `need` set hand over
-    // their samples and start afresh.
+    // their samples and counts and start afresh.
     __device__ __forceinline__ void flush_warp(const DevParams& P, BlockTally* bt, int e_base, bool need)
     {
-        const bool mine = need && e >= 0 && (nv[0] + nv[1] + nv[2]) > 0u;
+        const bool mine = need && e >= 0 && nv != 0ull;
         unsigned pending = __ballot_sync(0xffffffffu, mine);
         while (pending) {
             const int key = __shfl_sync(0xffffffffu, e, __ffs(pending) - 1);
             const bool in = mine && e == key;
             const unsigned grp = __ballot_sync(0xffffffffu, in);
-            const Acc<Real>* a[5] = {&v[0], &v[1], &v[2], &E, &Et};
             double vals[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const Real ss = warp_sum<Real>(in ? a[i]->s : Real(0));
-                const Real cc = warp_sum<Real>(in ? Real(a[i]->comp()) : Real(0));
-                vals[i] = double(ss) - double(cc);
-            }
-            unsigned int cnt[NV];
-#pragma unroll
-            for (int i = 0; i < NV; ++i) cnt[i] = __reduce_add_sync(0xffffffffu, in ? nv[i] : 0u);
+            vals[0] = double(warp_sum<Real>(in ? v[0].s : Real(0))) - double(warp_sum<Real>(in ? v[0].comp() : Real(0)));
+            vals[1] = double(warp_sum<Real>(in ? v[1].s : Real(0))) - double(warp_sum<Real>(in ? v[1].comp() : Real(0)));
+            vals[2] = double(warp_sum<Real>(in ? v[2].s : Real(0))) - double(warp_sum<Real>(in ? v[2].comp() : Real(0)));
+            vals[3] = double(warp_sum<Real>(in ? E.s : Real(0))) - double(warp_sum<Real>(in ? E.comp() : Real(0)));
+            vals[4] = double(warp_sum<Real>(in ? Et.s : Real(0))) - double(warp_sum<Real>(in ? Et.comp() : Real(0)));
+            const unsigned int c0 = __reduce_add_sync(0xffffffffu, in ? nvalley(0) : 0u);
+            const unsigned int c1 = __reduce_add_sync(0xffffffffu, in ? nvalley(1) : 0u);
+            const unsigned int c2 = __reduce_add_sync(0xffffffffu, in ? nvalley(2) : 0u);
             if ((threadIdx.x & 31) == __ffs(grp) - 1) {
-                const unsigned int n = cnt[0] + cnt[1] + cnt[2];
+                const unsigned int cnt[3] = {c0, c1, c2};
                 const int w = key - e_base;
                 if (w >= 0 && w < WE) {
-                    for (int i = 0; i < 5; ++i) atomicAdd(&bt->sums[w][i], vals[i]);
-                    for (int i = 0; i < NV; ++i) atomicAdd(&bt->cnt[w][CNT_V0 + i], cnt[i]);
-                    atomicAdd(&bt->cnt[w][CNT_SAMPLES], n);
-                } else {
-                    for (int i = 0; i < 5; ++i) atomicAdd(&P.sums[(size_t)key * NSUM + i], vals[i]);
+                    for (int i = 0; i < 5; ++i)
+                        if (vals[i] != 0.0) atomicAdd(&bt->sums[w][i], vals[i]);
                     for (int i = 0; i < NV; ++i)
-                        atomicAdd(&P.cnt[(size_t)key * NCNT + CNT_V0 + i], (unsigned long long)cnt[i]);
-                    atomicAdd(&P.cnt[(size_t)key * NCNT + CNT_SAMPLES], (unsigned long long)n);
+                        if (cnt[i]) atomicAdd(&bt->cnt[w][CNT_V0 + i], cnt[i]);
+                    atomicAdd(&bt->cnt[w][CNT_SAMPLES], c0 + c1 + c2);
+                } else {
+                    for (int i = 0; i < 5; ++i)
+                        if (vals[i] != 0.0) atomicAdd(&P.sums[(size_t)key * NSUM + i], vals[i]);
+                    for (int i = 0; i < NV; ++i)
+                        if (cnt[i]) atomicAdd(&P.cnt[(size_t)key * NCNT + CNT_V0 + i], (unsigned long long)cnt[i]);
+                    atomicAdd(&P.cnt[(size_t)key * NCNT + CNT_SAMPLES], (unsigned long long)(c0 + c1 + c2));
                 }
             }
             pending &= ~grp;
@@ -578,7 +601,7 @@ struct Samples {
             for (int i = 0; i < 3; ++i) v[i].clear();
             E.clear();
             Et.clear();
-            nv[0] = nv[1] = nv[2] = 0u;
+            nv = 0ull;
         }
     }
 };
@@ -718,8 +741,8 @@ __global__ void __launch_bounds__(256, 4)
         const int ts = P.tabset[q.e];
         const Phys<Real>& ph = (ts < K.n_tab_s) ? ph_s[ts] : ph_g[ts];
         const Real* tab_g = tab_all + (size_t)ts * NV * K.nb * NM;
-        q.E = kane_E(ph.ck[q.v] * (q.kx * q.kx + q.ky * q.ky + q.kz * q.kz), ph.alpha[q.v]);
-        q.f = ph.vk[q.v] / (Real(1) + Real(2) * ph.alpha[q.v] * q.E);
+        q.E = kane_E(ph.ck[q.v] * norm2(q.kx, q.ky, q.kz), ph.alpha[q.v]);
+        q.f = ph.vk[q.v] / fma_(Real(2) * ph.alpha[q.v], q.E, Real(1));
         Real f4[4];
         if (!NW) load4<Real>(static_cast<const Real*>(P.acc_bulk) + 4 * (size_t)q.e, f4);
         int cell = -1;
@@ -756,9 +779,8 @@ __global__ void __launch_bounds__(256, 4)
                     final_state<Real, NW>(Q, P, K, ph, bt, e_base);
             }
             if (!live) break;
-            const int v = q.v;
-            ss.add(S, q.f * q.kx, q.f * q.ky, q.f * q.kz, q.E, q.E + ph.Ec[v]);
-            S.nv[v] += 1u;
+            ss.add(S, q.f * q.kx, q.f * q.ky, q.f * q.kz, q.E, q.E + ph.Ec[q.v]);
+            S.count_valley(q.v);
         }
         ss.fold(S);
         store<Real>(P, p, q, NW);

@@ -188,13 +188,14 @@ def reduce_over_ranks(world: int, times: list, counts: list, device=None) -> tup
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(n_particles: int, steps: int, min_seconds: float = 0.0) -> dict:
-    """The FP64 oracle as it stands, single thread, on one bias point of the
-    sweep (V_d = 10 V): real scattering events per second over `steps`
-    Poisson periods (continuing until min_seconds if given)."""
+def oracle_sample(n_particles: int, steps: int, min_seconds: float = 0.0, threads: int = 1) -> dict:
+    """The FP64 oracle as it stands on one bias point of the sweep (V_d =
+    10 V), its particle loop on `threads` host threads: real scattering
+    events per second over `steps` Poisson periods (continuing until
+    min_seconds if given)."""
     from oracle import oracle
     cfg = W.nanowire(n_particles=n_particles, Vd=10.0, seed=10)
-    sim = oracle.Sim(cfg)
+    sim = oracle.Sim(cfg, threads=threads)
     t0 = sim.tallies()
     start = time.perf_counter()
     done = 0
@@ -204,7 +205,7 @@ def oracle_sample(n_particles: int, steps: int, min_seconds: float = 0.0) -> dic
     el = time.perf_counter() - start
     t1 = sim.tallies()
     ev = int(t1["events"].sum()) - int(t0["events"].sum())
-    return {"events": ev, "seconds": el, "periods": done, "n_particles": n_particles}
+    return {"events": ev, "seconds": el, "periods": done, "n_particles": n_particles, "threads": threads}
 
 
 def run_reference(args, world: int, rank: int):
@@ -213,8 +214,9 @@ def run_reference(args, world: int, rank: int):
     n_ref = 200_000 if args.steps + args.warmup <= 400 else max(20_000, int(200_000 * 400 / (args.steps + args.warmup)))
     from oracle import oracle
     oracle.build()
+    cores = oracle.host_cores()
     cfg = W.nanowire(n_particles=n_ref, Vd=10.0, seed=10)
-    sim = oracle.Sim(cfg)
+    sim = oracle.Sim(cfg, threads=cores)
     sim.run(STEPS_PER_POISSON * args.warmup)
     t0 = sim.tallies()
     start = time.perf_counter()
@@ -223,14 +225,14 @@ def run_reference(args, world: int, rank: int):
     t1 = sim.tallies()
     ev = int(t1["events"].sum()) - int(t0["events"].sum())
     value = ev / el
-    sample = ("FP64 oracle, single thread: 1 of the 21 bias points (V_d = 10 V), %d superparticles, "
-              "each step one Poisson period (10 x 1 fs)" % n_ref)
+    sample = ("FP64 oracle, particle loop on all %d host cores: 1 of the 21 bias points (V_d = 10 V), "
+              "%d superparticles, each step one Poisson period (10 x 1 fs)" % (cores, n_ref))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_desc(200_000),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -239,11 +241,19 @@ def run_reference(args, world: int, rank: int):
 # ------------------------------------------------- surrogate vs plain MC
 def electrothermal_comparison(args, stream) -> dict:
     """Convergence of the coupled electrothermal iteration on the half
-    nanowire at 64 drain biases (0..20 V) with 1800 subcells: plain Monte
-    Carlo from a uniform 300 K start vs the surrogate warm start (surrogate
-    trained on this library's own bulk Monte Carlo data, its data and
-    training time counted separately).  Peak temperature rises are compared
-    at convergence, where the Monte Carlo decides the result."""
+    nanowire at 64 drain biases (0..20 V) with 1800 subcells, four ways,
+    each from the same steady 300 K electron state: the plain Monte Carlo
+    iteration from a uniform 300 K start; the surrogate warm start (the
+    first Fourier step corrected by the surrogate's v_d(E, T), which rescales
+    each subcell's heat for the temperature it will have, then the plain
+    iteration); the surrogate-corrected iteration (that correction in every
+    Fourier step); and the plain iteration started from the surrogate's own
+    heat map (heat per electron at each subcell's field x the subcell's
+    electron density -> Fourier).  Every loop stops
+    when no subcell temperature changes by more than max(0.1 K, the Monte
+    Carlo noise of the iteration), and every result is then judged by one
+    long plain Monte Carlo window + Fourier solve at the temperatures the
+    loop returned; the peak rises compared are the judge's."""
     import numpy as np
     import paper_1707_09073_gb300 as emc
     from paper_1707_09073_gb300 import electrothermal as ET
@@ -270,60 +280,89 @@ def electrothermal_comparison(args, stream) -> dict:
     # kappa(T) with the phonon-electron scattering of Eq. (1) at the wire's
     # doping (1e18 cm^-3)
     tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=args.h_bottom, L_boundary=120e-9, tol_K=1e-3,
-                                n_e=cfgs[0]["Nd"], elec=W.ELECTRON_PHONON_GAN)
+                                n_e=cfgs[0]["Nd"], elec=W.ELECTRON_PHONON_GAN, substrate=W.TABLE_II_SIC,
+                                area_ratio=args.interface_area_ratio)
+    # the kappa and interface tables are built once per process (cached):
+    # build them before any loop is timed
+    emc.emc.kappa(tc, [300.0])
+    emc.emc.interface_conductance(tc, [300.0])
     out = {}
-    for mode in ("plain", "surrogate"):
+    for mode in ("plain", "surrogate_warm_start", "surrogate", "surrogate_heat_start"):
         ctx = emc.Context(cfgs, stream=stream.cuda_stream)
         try:
-            # electrons first reach steady state at 300 K (the same for both
-            # runs; not part of the convergence comparison)
             ss = ET.warm_to_steady(ctx)
             t0 = time.perf_counter()
             T0 = np.full((nb, ctx.n_cell), 300.0)
             if mode == "plain":
-                r = ET.iterate(ctx, tc, T0, max_iter=15, rtol=0.01)
-                t_sur = 0.0
+                r = ET.iterate(ctx, tc, T0, max_iter=15, stop_K=0.1)
+            elif mode == "surrogate_warm_start":
+                r = ET.surrogate_accelerated(ctx, sur, tc, T0, max_iter=15, stop_K=0.1, corrected_iters=1)
+            elif mode == "surrogate":
+                r = ET.surrogate_accelerated(ctx, sur, tc, T0, max_iter=15, stop_K=0.1)
             else:
-                r = ET.surrogate_accelerated(ctx, sur, tc, T0, max_iter=15, rtol=0.01)
-                t_sur = r["surrogate_seconds"]
-            out.setdefault("warmup", {})[mode] = {"steady": ss["steady"], "windows_of_200_steps": ss["windows"]}
-            if mode == "plain":
-                # Fig. 5 quantity: peak rise / emitted phonon power; half wire
-                # as simulated, and the 31-wire array of identical wires
-                # (each full wire emits twice the half wire's power)
-                pts = []
-                for i in range(0, nb, max(1, (nb - 1) // 8)):
-                    R = float(r["R_th_K_per_W"][i])
-                    if R == R:
-                        pts.append({"Vd": cfgs[i]["Vd"], "peak_rise_K": float(r["peak"][i]),
-                                    "power_W_half_wire": float(r["power_W"][i]), "R_th_K_per_W_half_wire": R,
-                                    "R_th_K_per_W_array31": R / (2.0 * 31.0)})
-                out["R_th_vs_Vd"] = pts
-            out[mode] = {"converged": r["converged"], "mc_iterations": r["iterations"],
-                         "seconds": time.perf_counter() - t0, "surrogate_seconds": t_sur,
-                         "peak_rise_K_max_bias": float(r["peak"][-1]),
+                T0 = ET.surrogate_heat_start(ctx, sur, tc)
+                r = ET.iterate(ctx, tc, T0, max_iter=15, stop_K=0.1)
+            secs = time.perf_counter() - t0
+            j = ET.judge(ctx, tc, r["T"], avg_steps=args.et_judge_steps)
+            out[mode] = {"converged": r["converged"], "mc_iterations": r["iterations"], "seconds": secs,
+                         "surrogate_seconds": r.get("surrogate_seconds", 0.0),
                          "peak_rise_K_max_bias_history": [round(float(h[-1]), 2) for h in r["history"]],
-                         "peak": r["peak"]}
+                         "max_dT_K_history": [round(x, 3) for x in r["max_dT_K"]],
+                         "noise_K_history": [round(x, 3) for x in r["noise_K"]],
+                         "judge_peak_rise_K_max_bias": float(j["peak"][-1]),
+                         "judge_peak_se_K_max_bias": float(j["peak_se"][-1]),
+                         "judge_max_dT_K": float(j["max_dT_K"].max()),
+                         "steady_start": {"steady": ss["steady"], "windows_of_200_steps": ss["windows"]},
+                         "_judge": j, "_r": r}
         finally:
             ctx.close()
-    dp = out["surrogate"]["peak"] - out["plain"]["peak"]
-    hot = out["plain"]["peak"] > 1.0
+    plain = out["plain"]["_judge"]
+    hot = plain["peak"] >= 5.0
+    cmp = {}
+    for mode in ("surrogate_warm_start", "surrogate", "surrogate_heat_start"):
+        jm = out[mode]["_judge"]
+        d = jm["peak"] - plain["peak"]
+        se = np.hypot(jm["peak_se"], plain["peak_se"])
+        rel = np.abs(d[hot]) / plain["peak"][hot]
+        cmp[mode] = {"max_rel_diff_peak_rise": float(rel.max()), "mean_rel_diff_peak_rise": float(rel.mean()),
+                     "biases_within_1pct": int((rel <= 0.01).sum()), "biases_compared": int(hot.sum()),
+                     "biases_within_1pct_or_3se": int(((np.abs(d) <= np.maximum(0.01 * plain["peak"], 3 * se))[hot]).sum()),
+                     "max_abs_diff_K_cool_biases": float(np.abs(d[~hot]).max()) if (~hot).any() else None,
+                     "speedup_vs_plain": out["plain"]["seconds"] / max(out[mode]["seconds"], 1e-9)}
+    saving = out["plain"]["seconds"] - out["surrogate_warm_start"]["seconds"]
+    rth = []
+    for i in range(0, nb, max(1, (nb - 1) // 8)):
+        R = float(plain["R_th_K_per_W"][i])
+        if R == R:
+            rth.append({"Vd": cfgs[i]["Vd"], "peak_rise_K": float(plain["peak"][i]),
+                        "power_W_half_wire": float(plain["power_W"][i]), "R_th_K_per_W_half_wire": R,
+                        "R_th_K_per_W_array31": R / (2.0 * 31.0)})
     res = {
         "workload": "half nanowire 3x6x100, %d drain biases 0..20 V x %d superparticles, Fourier with kappa(T) "
                     "(Table II, 120 nm boundary, phonon-electron scattering of Eq. (1) at 1e18 cm^-3), "
-                    "h_bottom %.1e W/m2/K; converged when every peak rise changes "
-                    "< max(1%%, 0.5 K) between iterations; both runs start from a steady 300 K "
-                    "electron state; surrogate run: after every Monte Carlo run the Fourier solve is iterated with "
-                    "the heat rescaled by the surrogate's v_d(E, T) / v_d(E, T_MC) per subcell" % (nb, args.et_particles, args.h_bottom),
-        "plain_mc": {k: v for k, v in out["plain"].items() if k != "peak"},
-        "surrogate_warm_start": {k: v for k, v in out["surrogate"].items() if k != "peak"},
-        "R_th_vs_Vd": out.get("R_th_vs_Vd"),
-        "warmup_to_steady_state": out.get("warmup"),
-        "speedup": out["plain"]["seconds"] / max(out["surrogate"]["seconds"], 1e-9),
-        "peak_rise_max_rel_diff": float(np.max(np.abs(dp[hot]) / out["plain"]["peak"][hot])) if hot.any() else None,
-        "peak_rise_rel_diff_max_bias": float(abs(dp[-1]) / max(out["plain"]["peak"][-1], 1e-9)),
-        "surrogate": {"samples": args.sur_samples, "data_seconds": t_data, "train_seconds": t_train,
-                      "train_steps": 3000, "batch": 1024, "infer_ms_115200_queries": 1e3 * t_infer,
+                    "bottom face on the GaN/SiC interface of Eqs. (2)-(3) (diffuse mismatch, Table II "
+                    "dispersions, R_K(300 K) = %.3g m2K/W) over %g times the wire's footprint%s; "
+                    "each loop stops when no subcell temperature changes by more than "
+                    "max(0.1 K, the largest difference between the temperatures of the two half-window heat maps); "
+                    "every result judged by a %d-step plain Monte Carlo window + Fourier solve"
+                    % (nb, args.et_particles, 1.0 / float(emc.emc.interface_conductance(tc, [300.0])[0]),
+                       args.interface_area_ratio,
+                       ("" if args.h_bottom <= 0 else ", lumped %.1e W/m2/K in series" % args.h_bottom),
+                       args.et_judge_steps),
+        "plain_mc": {k: v for k, v in out["plain"].items() if not k.startswith("_")},
+        "surrogate_warm_start": {k: v for k, v in out["surrogate_warm_start"].items() if not k.startswith("_")},
+        "surrogate_corrected": {k: v for k, v in out["surrogate"].items() if not k.startswith("_")},
+        "surrogate_heat_start": {k: v for k, v in out["surrogate_heat_start"].items() if not k.startswith("_")},
+        "judged_peak_rise_vs_plain": cmp,
+        "speedup": out["plain"]["seconds"] / max(out["surrogate_warm_start"]["seconds"], 1e-9),
+        "mc_iterations": {m: out[m]["mc_iterations"] for m in out},
+        "R_th_vs_Vd": rth,
+        "cost": {"surrogate_data_seconds": t_data, "surrogate_train_seconds": t_train,
+                 "saving_per_run_seconds": saving,
+                 "break_even_runs": (t_data + t_train) / saving if saving > 0 else None,
+                 "note": "the surrogate is trained once per material and doping range and reused by every sweep"},
+        "surrogate": {"samples": args.sur_samples, "train_steps": 3000, "batch": 1024,
+                      "infer_ms_115200_queries": 1e3 * t_infer,
                       "network": "4-128-128-128-7 SiLU, BF16 tcgen05 tensor cores, FP32 accumulation in TMEM"},
     }
     return res
@@ -513,10 +552,15 @@ def run_emc(args, world: int, rank: int, local: int):
     if world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
         oracle.build()
-        s = oracle_sample(args.cpu_particles, steps=2, min_seconds=args.cpu_seconds)
-        cpu = {"value": s["events"] / s["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 oracle, single thread: 1 of the 21 bias points (V_d = 10 V), %d superparticles, "
-                         "%d Poisson periods (%.1f s)" % (s["n_particles"], s["periods"], s["seconds"])}
+        cores = oracle.host_cores()
+        s = oracle_sample(args.cpu_particles, steps=2, min_seconds=args.cpu_seconds, threads=cores)
+        s1 = oracle_sample(args.cpu_particles, steps=1, min_seconds=args.cpu_seconds / 4, threads=1)
+        cpu = {"value": s["events"] / s["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle, particle loop on all %d host cores: 1 of the 21 bias points (V_d = 10 V), "
+                         "%d superparticles, %d Poisson periods (%.1f s)" % (cores, s["n_particles"], s["periods"],
+                                                                             s["seconds"]),
+               "single_thread": {"value": s1["events"] / s1["seconds"], "unit": UNIT, "cores": 1,
+                                 "sample": "%d Poisson periods (%.1f s)" % (s1["periods"], s1["seconds"])}}
 
     mixed = None
     if world == 1 and not args.no_batched:
@@ -574,8 +618,12 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
+    ap.add_argument("--et-judge-steps", type=int, default=5000)
     ap.add_argument("--sur-samples", type=int, default=100_000)
-    ap.add_argument("--h-bottom", type=float, default=5e8)
+    ap.add_argument("--h-bottom", type=float, default=0.0,
+                    help="lumped conductance under the interface, W/m2/K (0: none)")
+    ap.add_argument("--interface-area-ratio", type=float, default=10.0,
+                    help="GaN/SiC interface area per unit of the wire's bottom face")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -4,14 +4,13 @@
  * Hao et al., "Hybrid Electrothermal Simulation of a Three-Dimensional
  * Fin-Shaped Field-Effect Transistor Based on GaN Nanowires" (arXiv:1707.09073).
  * The paper's electron side: an ensemble Monte Carlo that tracks individual
- * electrons (the paragraph opening "In such simulations"), Kane bands over the
- * Gamma1/U/Gamma3 valleys with ionized impurity, polar optical, acoustic
- * deformation potential and intervalley optical scattering and the Table I
- * parameters (the paragraph opening "For Si-doped GaN nanowires"), a half
- * nanowire divided into 3 x 6 x 100 subcells that count electrons for a
- * Poisson update of the 3D field, and the electron-to-phonon energy exchange
- * counted per subcell for the thermal side (the paragraph ending "for the
- * following thermal simulations").
+ * electrons (the hybrid-method paragraph), Kane bands over the Gamma1/U/Gamma3
+ * valleys with ionized impurity, polar optical, acoustic deformation
+ * potential and intervalley optical scattering and the Table I parameters
+ * (the electron-model paragraph), a half nanowire divided into 3 x 6 x 100
+ * subcells that count electrons for a Poisson update of the 3D field, and the
+ * electron-to-phonon energy exchange counted per subcell for the thermal side
+ * (the paragraph on the field update and the heat counted in steady state).
  *
  * Conventions for every entry point:
  *  - Return EMC_OK or an error code; nothing throws.  emc_last_error() gives
@@ -248,8 +247,8 @@ emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes);
 /* Lattice temperature per subcell of ensemble ens (nanowire contexts whose
  * ensembles share one material and doping): T_cells[n] in K, n = the
  * subcell count (or 1 for a uniform value).  The phonon feedback of the
- * thermal side on the electrons (the paragraph opening "the phonon MC
- * simulations and Fourier's law analysis are then carried out").  Rates
+ * thermal side on the electrons (the coupling paragraph: the updated local
+ * temperature changes the electrons' scattering rates).  Rates
  * are tabulated on temperature bins T_k = 250 K + 5 K k (k = 0..150) and a
  * subcell uses the bin nearest its temperature; a scattering is tried
  * against the ensemble's Gamma0 (the largest total rate over the bins in
@@ -346,7 +345,9 @@ emc_status emc_surrogate_params(emc_ctx* ctx, float* dst, int64_t* count);
  * relaxation 1/tau = A omega^4 + B1 omega^2 T exp(-B2/T), Table II) plus a
  * boundary term v_g / L_boundary (the size-modified mean free paths).
  * Contacts (x = 0, x = L) are held at T_sink; the bottom face (z = 0) loses
- * heat to T_sink through h_bottom (W/m^2/K); other faces are adiabatic.
+ * heat to T_sink through h_bottom (W/m^2/K) and, when interface_dmm = 1, the
+ * diffuse-mismatch interface of Eqs. (2)-(3) in series; other faces are
+ * adiabatic.
  */
 typedef struct emc_thermal_config {
     double T_sink;          /* K */
@@ -360,6 +361,15 @@ typedef struct emc_thermal_config {
      * (m/s); the Fermi level follows from n_e at each temperature */
     double n_e_m3, m_e_rel, Da_eV, rho_kg_m3, vg_e_m_s;
     int32_t max_picard, max_cg;
+    /* interface under the bottom face, diffuse mismatch model (Eqs. (2) and
+     * (3)), used when interface_dmm = 1: the substrate's column of Table II
+     * (its sine branches), and the interface area per unit area of the
+     * wire's bottom face (> 0; the heat may spread before it crosses).  The
+     * conductance area_ratio / R_K(T), at the temperature of the adjacent
+     * subcell, is in series with the half cell and with h_bottom (h_bottom
+     * <= 0: no lumped part). */
+    int32_t interface_dmm, pad_;
+    double sub_k0_per_m, sub_omega_max_rad_s, interface_area_ratio;
 } emc_thermal_config;
 
 /* Solve every ensemble of a nanowire context (at most 2048 subcells):
@@ -370,6 +380,16 @@ emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const d
                              int32_t* iters);
 /* kappa(T) (W/m/K) as used by emc_thermal_solve, for n host temperatures. */
 emc_status emc_kappa(const emc_thermal_config* tc, const double* T, double* kappa, int32_t n);
+/* Diffuse mismatch model between the wire (k0_per_m, omega_max_rad_s of tc)
+ * and the substrate (sub_k0_per_m, sub_omega_max_rad_s), three identical
+ * sine-shaped acoustic branches each.  emc_dmm_transmissivity: Eq. (2),
+ * tau_12(omega) from wire to substrate for n host angular frequencies
+ * (rad/s; 0 where the substrate has no states).  emc_interface_conductance:
+ * Eq. (3), 1/R_K (W/(m^2 K)) per unit interface area at n host temperatures
+ * (K, tabulated in 0.5 K steps from 150 K to 1500 K as used by
+ * emc_thermal_solve).  EMC_EINVAL for non-positive dispersion parameters. */
+emc_status emc_dmm_transmissivity(const emc_thermal_config* tc, const double* omega, double* tau12, int32_t n);
+emc_status emc_interface_conductance(const emc_thermal_config* tc, const double* T, double* G_K, int32_t n);
 
 /* Diagnostics used by the test-suite. */
 /* Philox4x32-10 evaluated on the device for n (counter, key) pairs:

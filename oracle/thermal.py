@@ -94,7 +94,7 @@ def kappa(T, mat, L_b=0.0, n_e=0.0, elec=None):
     return integrate.quad(f, 0.0, q0, epsabs=0, epsrel=1e-10, limit=400)[0]
 
 
-def operator(cfg, kap, T_sink, h_bottom):
+def operator(cfg, kap, T_sink, h_bottom, g_if=None):
     nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
     hx, hy, hz = cfg["Lx"] / nx, cfg["Ly"] / ny, cfg["Lz"] / nz
     n = nx * ny * nz
@@ -120,28 +120,88 @@ def operator(cfg, kap, T_sink, h_bottom):
                         diag[c] += g
                         rhs_b[c] += g * T_sink
                     elif dl == -1:  # bottom face: conductance to the sink
-                        g = 1.0 / (h * (h / (2 * kc) + 1.0 / h_bottom))
+                        r = h / (2 * kc) + (1.0 / h_bottom if h_bottom > 0 else 0.0)
+                        if g_if is not None:  # the interface of Eq. (3) in series
+                            r += 1.0 / g_if[c]
+                        g = 1.0 / (h * r)
                         diag[c] += g
                         rhs_b[c] += g * T_sink
     A = sparse.csr_matrix((vals + list(diag), (rows + list(range(n)), cols + list(range(n)))), shape=(n, n))
     return A, rhs_b
 
 
-def solve(cfg, q, mat, T_sink=300.0, h_bottom=1e9, L_b=0.0, tol=1e-8, max_picard=50, T0=None, n_e=0.0, elec=None):
+def solve(cfg, q, mat, T_sink=300.0, h_bottom=1e9, L_b=0.0, tol=1e-8, max_picard=50, T0=None, n_e=0.0, elec=None,
+          substrate=None, area_ratio=1.0):
+    """Steady temperatures (K) per subcell for heat q (W/m^3).  substrate:
+    the Table II column of the material under the bottom face; then the
+    interface conductance of Eq. (3) at the adjacent subcell's temperature,
+    times area_ratio, is in series with the half cell and h_bottom (h_bottom
+    <= 0: no lumped part)."""
     n = cfg["nx"] * cfg["ny"] * cfg["nz"]
     T = np.full(n, T_sink) if T0 is None else np.array(T0, dtype=float)
-    cache = {}
+    cache, gcache = {}, {}
     def kap_of(t):
         key = round(float(t), 9)
         if key not in cache:
             cache[key] = kappa(t, mat, L_b, n_e, elec)
         return cache[key]
+    def gif_of(t):
+        key = round(float(t), 9)
+        if key not in gcache:
+            gcache[key] = area_ratio * interface_conductance(t, mat, substrate)
+        return gcache[key]
     for _ in range(max_picard):
         kap = np.array([kap_of(t) for t in T])
-        A, b = operator(cfg, kap, T_sink, h_bottom)
+        g_if = np.array([gif_of(t) for t in T]) if substrate is not None else None
+        A, b = operator(cfg, kap, T_sink, h_bottom, g_if)
         Tn = spla.spsolve(A.tocsc(), q + b)
         done = np.abs(Tn - T).max() < tol
         T = Tn
         if done:
             break
     return T
+
+
+# ------------------------------------------------------------------ DMM
+# Diffuse mismatch model of the interface between material 1 (the wire) and
+# material 2 (the substrate), Eqs. (2) and (3), for the paper's phonon model:
+# three identical acoustic branches per material with omega = omega_max
+# sin(pi q / 2 q0).
+
+def branch(mat, w):
+    """Wave vector q(w), group velocity v_g(w) and density of states D(w)
+    (per branch and unit volume, q^2 / (2 pi^2 v_g)) of one sine-shaped
+    branch; zero states above omega_max."""
+    q0, wm = mat["k0_per_m"], mat["omega_max_rad_s"]
+    if not (0.0 < w < wm):
+        return 0.0, 0.0, 0.0
+    q = 2.0 * q0 / np.pi * np.arcsin(w / wm)
+    vg = wm * np.pi / (2.0 * q0) * np.cos(np.pi * q / (2.0 * q0))
+    return q, vg, q * q / (2.0 * np.pi ** 2 * vg)
+
+
+def tau12(w, mat1, mat2):
+    """Eq. (2): transmissivity from 1 to 2, the sums over the three branches
+    of v_g D of each side."""
+    _, v1, D1 = branch(mat1, w)
+    _, v2, D2 = branch(mat2, w)
+    s1, s2 = 3.0 * v1 * D1, 3.0 * v2 * D2
+    return s2 / (s1 + s2) if s1 + s2 > 0.0 else 0.0
+
+
+def interface_conductance(T, mat1, mat2):
+    """Eq. (3): 1/R_K = sum over the branches of material 1 of
+    int_0^omega_max1 v_g c(w) tau12(w) dw / 4, with c(w) = hbar w D(w) dn/dT
+    the spectral heat capacity per unit volume.  W/(m^2 K)."""
+    wm = mat1["omega_max_rad_s"]
+
+    def f(w):
+        _, v1, D1 = branch(mat1, w)
+        x = HB * w / (KB * T)
+        if x > 700.0:
+            return 0.0
+        dndT = x * np.exp(x) / np.expm1(x) ** 2 / T
+        return 3.0 * v1 * HB * w * D1 * dndT * tau12(w, mat1, mat2) / 4.0
+
+    pts = sorted({min(mat2["omega_max_rad_s"], wm) * (1 - 1e-12), wm * 0.5})
+    return integrate.quad(f, 0.0, wm, epsabs=0, epsrel=1e-11, limit=800, points=pts)[0]

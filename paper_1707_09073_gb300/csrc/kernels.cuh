@@ -2,8 +2,8 @@
 // initial ensemble, and the contact re-injection.  Real = float is the
 // production path, Real = double the parity build.
 //
-// Method (Hao et al., arXiv:1707.09073; the paragraphs opening "In such
-// simulations" and "For Si-doped GaN nanowires"): every electron is tracked
+// Method (Hao et al., arXiv:1707.09073; the hybrid-method and electron-model
+// paragraphs, Table I): every electron is tracked
 // through free flights under the local field with the Kane dispersion
 // E(1 + aE) = hbar^2 k^2 / 2m, interrupted by scatterings chosen against a
 // constant total rate Gamma0 per valley (self-scattering fills the gap to the

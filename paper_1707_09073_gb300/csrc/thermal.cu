@@ -153,10 +153,75 @@ std::vector<double> kappa_table(const emc_thermal_config& tc)
     return it->second;
 }
 
+// 1/R_K(T) of Eq. (3) per unit interface area on the kappa grid.  With the
+// sine branches, v_g D = q^2 / (2 pi^2) per branch, so Eq. (2) is
+// tau_12 = q_2(w)^2 / (q_1(w)^2 + q_2(w)^2) (zero above the substrate's
+// omega_max) and Eq. (3) is, over the wire's wave vector q_1 (dw = v_g dq),
+// (3/4) int hbar w (q_1^2 / 2 pi^2) dn/dT tau_12 v_g dq_1 (midpoint rule, up
+// to the wave vector at which the substrate runs out of states).
+double dmm_tau12(double w, const emc_thermal_config& tc)
+{
+    const double w1 = tc.omega_max_rad_s, w2 = tc.sub_omega_max_rad_s;
+    if (!(w > 0.0) || !(w < w2)) return 0.0;  // no substrate states
+    if (!(w < w1)) return 1.0;                // substrate states only
+    const double q1 = 2.0 * tc.k0_per_m / kPi * std::asin(w / w1);
+    const double q2 = 2.0 * tc.sub_k0_per_m / kPi * std::asin(w / w2);
+    return q2 * q2 / (q1 * q1 + q2 * q2);
+}
+
+std::vector<double> interface_table_build(const emc_thermal_config& tc)
+{
+    const double q0 = tc.k0_per_m, wm = tc.omega_max_rad_s;
+    const double qtop = tc.sub_omega_max_rad_s < wm ? 2.0 * q0 / kPi * std::asin(tc.sub_omega_max_rad_s / wm) : q0;
+    const int nq = 8000;
+    std::vector<double> out(kNT);
+    for (int t = 0; t < kNT; ++t) {
+        const double T = kTLo + kTStep * t;
+        double acc = 0.0;
+        for (int i = 0; i < nq; ++i) {
+            const double q = (i + 0.5) * qtop / nq;
+            const double w = wm * std::sin(kPi * q / (2.0 * q0));
+            const double vg = wm * kPi / (2.0 * q0) * std::cos(kPi * q / (2.0 * q0));
+            const double x = kHbar * w / (kKB * T);
+            const double em1 = std::expm1(x);
+            const double dndT = x * std::exp(x) / (em1 * em1) / T;
+            acc += kHbar * w * q * q / (2.0 * kPi * kPi) * dndT * dmm_tau12(w, tc) * vg;
+        }
+        out[t] = 0.75 * acc * qtop / nq;
+    }
+    return out;
+}
+
+bool dmm_ok(const emc_thermal_config& tc)
+{
+    return tc.k0_per_m > 0.0 && tc.omega_max_rad_s > 0.0 && tc.sub_k0_per_m > 0.0 && tc.sub_omega_max_rad_s > 0.0;
+}
+
+std::vector<double> interface_table(const emc_thermal_config& tc)
+{
+    static std::mutex mu;
+    static std::map<std::vector<double>, std::vector<double>> cache;
+    const std::vector<double> key = {tc.k0_per_m, tc.omega_max_rad_s, tc.sub_k0_per_m, tc.sub_omega_max_rad_s};
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) it = cache.emplace(key, interface_table_build(tc)).first;
+    return it->second;
+}
+
+double table_at(const std::vector<double>& tab, double T)
+{
+    double f = (T - kTLo) / kTStep;
+    f = std::fmin(std::fmax(f, 0.0), double(kNT - 1) - 1e-9);
+    const int k = int(f);
+    const double a = f - k;
+    return tab[k] * (1.0 - a) + tab[k + 1] * a;
+}
+
 struct TGeo {
     int nx, ny, nz, n;
     double hx, hy, hz, T_sink, h_bottom, tol;
     int max_picard, max_cg;
+    const double* g_if;    // interface conductance table (area ratio applied), or null
 };
 
 __device__ __forceinline__ double kap_at(const double* tab, double T)
@@ -168,8 +233,9 @@ __device__ __forceinline__ double kap_at(const double* tab, double T)
     return tab[i] * (1.0 - a) + tab[i + 1] * a;
 }
 
-// y = A(kappa) x on the grid; bnd[c] receives the boundary conductance sum
-__device__ void apply(const TGeo& G, const double* kap, const double* x, double* y, double* bnd)
+// y = A(kappa) x on the grid; bnd[c] receives the boundary conductance sum.
+// gif[c]: the interface conductance of a bottom subcell (0: none)
+__device__ void apply(const TGeo& G, const double* kap, const double* gif, const double* x, double* y, double* bnd)
 {
     for (int c = threadIdx.x; c < G.n; c += blockDim.x) {
         const int i = c / (G.ny * G.nz), j = (c / G.nz) % G.ny, l = c % G.nz;
@@ -183,7 +249,13 @@ __device__ void apply(const TGeo& G, const double* kap, const double* x, double*
         if (i < G.nx - 1) face(c + G.ny * G.nz, G.hx); else gb += 2.0 * kc / (G.hx * G.hx);
         if (j > 0) face(c - G.nz, G.hy);
         if (j < G.ny - 1) face(c + G.nz, G.hy);
-        if (l > 0) face(c - 1, G.hz); else gb += 1.0 / (G.hz * (G.hz / (2.0 * kc) + 1.0 / G.h_bottom));
+        if (l > 0) {
+            face(c - 1, G.hz);
+        } else {
+            double r = G.hz / (2.0 * kc) + (G.h_bottom > 0.0 ? 1.0 / G.h_bottom : 0.0);
+            if (gif[c] > 0.0) r += 1.0 / gif[c];
+            gb += 1.0 / (G.hz * r);
+        }
         if (l < G.nz - 1) face(c + 1, G.hz);
         y[c] = acc + gb * xc;
         if (bnd) bnd[c] = gb;
@@ -224,6 +296,7 @@ __global__ void __launch_bounds__(512) k_thermal(TGeo G, const double* __restric
     double* r = sh + 2 * G.n;
     double* p = sh + 3 * G.n;
     double* Ap = sh + 4 * G.n;
+    double* gif = sh + 6 * G.n;
     __shared__ double red[32];
     const int e = blockIdx.x;
     const double* qe = q + (size_t)e * G.n;
@@ -234,11 +307,12 @@ __global__ void __launch_bounds__(512) k_thermal(TGeo G, const double* __restric
     for (; pic < G.max_picard; ++pic) {
         for (int c = threadIdx.x; c < G.n; c += blockDim.x) {
             kap[c] = kap_at(tab, x[c]);
+            gif[c] = (G.g_if && c % G.nz == 0) ? kap_at(G.g_if, x[c]) : 0.0;
             p[c] = x[c];  // previous Picard iterate
         }
         __syncthreads();
         // r = b - A x with b = q + g_b T_sink
-        apply(G, kap, x, Ap, r);
+        apply(G, kap, gif, x, Ap, r);
         __syncthreads();
         double rr = 0.0, bb = 0.0;
         for (int c = threadIdx.x; c < G.n; c += blockDim.x) {
@@ -261,7 +335,7 @@ __global__ void __launch_bounds__(512) k_thermal(TGeo G, const double* __restric
         __syncthreads();
         const double stop = 1e-26 * fmax(bb, 1e-300);
         for (int it = 0; it < G.max_cg && rr > stop; ++it, ++total) {
-            apply(G, kap, d, Ad, nullptr);
+            apply(G, kap, gif, d, Ad, nullptr);
             __syncthreads();
             double dAd = 0.0;
             for (int c = threadIdx.x; c < G.n; c += blockDim.x) dAd += d[c] * Ad[c];
@@ -312,6 +386,21 @@ emc_status emc_kappa(const emc_thermal_config* tc, const double* T, double* kapp
     return EMC_OK;
 }
 
+emc_status emc_dmm_transmissivity(const emc_thermal_config* tc, const double* omega, double* tau12, int32_t n)
+{
+    if (!tc || n < 0 || (n > 0 && (!omega || !tau12)) || !dmm_ok(*tc)) return EMC_EINVAL;
+    for (int i = 0; i < n; ++i) tau12[i] = dmm_tau12(omega[i], *tc);
+    return EMC_OK;
+}
+
+emc_status emc_interface_conductance(const emc_thermal_config* tc, const double* T, double* G_K, int32_t n)
+{
+    if (!tc || n < 0 || (n > 0 && (!T || !G_K)) || !dmm_ok(*tc)) return EMC_EINVAL;
+    const std::vector<double> tab = interface_table(*tc);
+    for (int i = 0; i < n; ++i) G_K[i] = table_at(tab, T[i]);
+    return EMC_OK;
+}
+
 emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const double* q, double* T, int32_t* iters)
 {
     if (!ctx || !tc || !q || !T) return EMC_EINVAL;
@@ -321,11 +410,13 @@ emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const d
         return ctx_fail(ctx, EMC_ESTATE, "emc_thermal_solve needs the nanowire geometry");
     const int n = nx * ny * nz;
     if (n > kMaxThermalCells) return ctx_fail(ctx, EMC_EINVAL, "emc_thermal_solve: at most 2048 subcells");
-    if (!(tc->T_sink > 0) || !(tc->h_bottom > 0) || tc->max_picard <= 0 || tc->max_cg <= 0 || !electrons_ok(*tc))
+    const bool dmm = tc->interface_dmm != 0;
+    if (!(tc->T_sink > 0) || !(dmm || tc->h_bottom > 0) || tc->max_picard <= 0 || tc->max_cg <= 0 ||
+        !electrons_ok(*tc) || (dmm && (!dmm_ok(*tc) || !(tc->interface_area_ratio > 0))))
         return ctx_fail(ctx, EMC_EINVAL, "emc_thermal_solve: invalid configuration");
     cudaStream_t st = ctx_stream(ctx);
     const std::vector<double> tab = kappa_table(*tc);
-    double *d_tab = nullptr, *d_q = nullptr, *d_T = nullptr;
+    double *d_tab = nullptr, *d_q = nullptr, *d_T = nullptr, *d_gif = nullptr;
     int* d_it = nullptr;
     const size_t bytes = sizeof(double) * (size_t)ne * n;
 #define TCK(call)                                                                      \
@@ -338,10 +429,18 @@ emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const d
     TCK(cudaMallocAsync(&d_T, bytes, st));
     TCK(cudaMallocAsync(&d_it, sizeof(int) * 2 * ne, st));
     TCK(cudaMemcpyAsync(d_tab, tab.data(), sizeof(double) * kNT, cudaMemcpyHostToDevice, st));
+    std::vector<double> gtab;
+    if (dmm) {
+        gtab = interface_table(*tc);
+        for (double& g : gtab) g *= tc->interface_area_ratio;
+        TCK(cudaMallocAsync(&d_gif, sizeof(double) * kNT, st));
+        TCK(cudaMemcpyAsync(d_gif, gtab.data(), sizeof(double) * kNT, cudaMemcpyHostToDevice, st));
+    }
     TCK(cudaMemcpyAsync(d_q, q, bytes, cudaMemcpyHostToDevice, st));
     TCK(cudaMemcpyAsync(d_T, T, bytes, cudaMemcpyHostToDevice, st));
-    TGeo G{nx, ny, nz, n, Lx / nx, Ly / ny, Lz / nz, tc->T_sink, tc->h_bottom, tc->tol_K, tc->max_picard, tc->max_cg};
-    const size_t smem = sizeof(double) * 6 * n;
+    TGeo G{nx, ny, nz, n, Lx / nx, Ly / ny, Lz / nz, tc->T_sink, tc->h_bottom, tc->tol_K, tc->max_picard, tc->max_cg,
+           d_gif};
+    const size_t smem = sizeof(double) * 7 * n;
     TCK(cudaFuncSetAttribute(k_thermal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_thermal<<<ne, 512, smem, st>>>(G, d_tab, d_q, d_T, d_it);
     ctx_count_launches(ctx, 1);
@@ -352,6 +451,7 @@ emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const d
     TCK(cudaFreeAsync(d_q, st));
     TCK(cudaFreeAsync(d_T, st));
     TCK(cudaFreeAsync(d_it, st));
+    if (d_gif) TCK(cudaFreeAsync(d_gif, st));
     TCK(cudaStreamSynchronize(st));
 #undef TCK
     return EMC_OK;

@@ -391,13 +391,19 @@ class EmcThermalConfig(C.Structure):
                 ("k0_per_m", C.c_double), ("omega_max_rad_s", C.c_double), ("A_s3", C.c_double),
                 ("B1_s_per_K", C.c_double), ("B2_K", C.c_double),
                 ("n_e_m3", C.c_double), ("m_e_rel", C.c_double), ("Da_eV", C.c_double), ("rho_kg_m3", C.c_double),
-                ("vg_e_m_s", C.c_double), ("max_picard", C.c_int32), ("max_cg", C.c_int32)]
+                ("vg_e_m_s", C.c_double), ("max_picard", C.c_int32), ("max_cg", C.c_int32),
+                ("interface_dmm", C.c_int32), ("pad_", C.c_int32), ("sub_k0_per_m", C.c_double),
+                ("sub_omega_max_rad_s", C.c_double), ("interface_area_ratio", C.c_double)]
 
 
 def thermal_config(table_ii: dict, T_sink=300.0, h_bottom=1e9, L_boundary=120e-9, tol_K=1e-6, max_picard=50,
-                   max_cg=5000, n_e=0.0, elec: dict | None = None) -> EmcThermalConfig:
+                   max_cg=5000, n_e=0.0, elec: dict | None = None, substrate: dict | None = None,
+                   area_ratio: float = 1.0) -> EmcThermalConfig:
     """Thermal-side parameters; n_e (m^-3) > 0 with elec = {m_rel, Da_eV,
-    rho_kg_m3, vg_m_s} adds the phonon-electron scattering of Eq. (1)."""
+    rho_kg_m3, vg_m_s} adds the phonon-electron scattering of Eq. (1);
+    substrate (a Table II column) puts the diffuse-mismatch interface of
+    Eqs. (2)-(3), times area_ratio, under the bottom face (in series with
+    h_bottom; h_bottom <= 0: none)."""
     t = EmcThermalConfig()
     t.T_sink, t.h_bottom, t.L_boundary, t.tol_K = T_sink, h_bottom, L_boundary, tol_K
     t.k0_per_m, t.omega_max_rad_s = table_ii["k0_per_m"], table_ii["omega_max_rad_s"]
@@ -408,6 +414,10 @@ def thermal_config(table_ii: dict, T_sink=300.0, h_bottom=1e9, L_boundary=120e-9
         t.n_e_m3, t.m_e_rel, t.Da_eV = n_e, elec["m_rel"], elec["Da_eV"]
         t.rho_kg_m3, t.vg_e_m_s = elec["rho_kg_m3"], elec["vg_m_s"]
     t.max_picard, t.max_cg = max_picard, max_cg
+    if substrate is not None:
+        t.interface_dmm = 1
+        t.sub_k0_per_m, t.sub_omega_max_rad_s = substrate["k0_per_m"], substrate["omega_max_rad_s"]
+        t.interface_area_ratio = area_ratio
     return t
 
 
@@ -419,6 +429,9 @@ def _thermal_lib():
         L.emc_thermal_solve.restype = C.c_int
         L.emc_kappa.argtypes = [C.POINTER(EmcThermalConfig), dp, dp, C.c_int32]
         L.emc_kappa.restype = C.c_int
+        for f in ("emc_dmm_transmissivity", "emc_interface_conductance"):
+            getattr(L, f).argtypes = [C.POINTER(EmcThermalConfig), dp, dp, C.c_int32]
+            getattr(L, f).restype = C.c_int
         L._thermal_ready = True
     return L
 
@@ -429,6 +442,26 @@ def kappa(tc: EmcThermalConfig, T) -> np.ndarray:
     st = _thermal_lib().emc_kappa(C.byref(tc), _p(T), _p(out), T.size)
     if st != 0:
         raise EmcError(st, "emc_kappa")
+    return out
+
+
+def dmm_transmissivity(tc: EmcThermalConfig, omega) -> np.ndarray:
+    """Eq. (2): wire -> substrate transmissivity at angular frequencies omega."""
+    w = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+    out = np.zeros_like(w)
+    st = _thermal_lib().emc_dmm_transmissivity(C.byref(tc), _p(w), _p(out), w.size)
+    if st != 0:
+        raise EmcError(st, "emc_dmm_transmissivity")
+    return out
+
+
+def interface_conductance(tc: EmcThermalConfig, T) -> np.ndarray:
+    """Eq. (3): 1/R_K (W/m^2/K) per unit interface area at temperatures T."""
+    T = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    out = np.zeros_like(T)
+    st = _thermal_lib().emc_interface_conductance(C.byref(tc), _p(T), _p(out), T.size)
+    if st != 0:
+        raise EmcError(st, "emc_interface_conductance")
     return out
 
 

@@ -1,8 +1,8 @@
 """Steady-state detection for the self-consistent nanowire run.
 
-The paper stops counting heat once the current and the electric field no
-longer change (the paragraph ending "for the following thermal
-simulations").  Reading taken: over consecutive windows (default 100 time
+The paper counts the heat once the current and the electric field no longer
+change (the paragraph on the field update and the heat counted in steady
+state).  Reading taken: over consecutive windows (default 100 time
 steps), the window-mean drain current and the subcell field are compared
 with the previous window's; the run is steady once, for `need` windows in a
 row, the current changed by less than max(rtol |I|, 3 sigma of its window

@@ -48,13 +48,15 @@ def test_thermal_solve_with_electron_scattering(emc):
     assert rise[0.0, cfg["Nd"]].max() > 1.02 * rise[0.0, 0.0].max()
 
 
-def test_electrothermal_warm_start(emc):
+def test_electrothermal_surrogate_gains(emc):
     """From a steady electron state, the plain Monte Carlo iteration and the
-    surrogate-corrected one both converge and reach the same peak
-    temperature rise (within 3% or the Monte Carlo noise): the surrogate
-    changes the path of the iteration, not the fixed point it ends at.  The
-    iteration counts and times of both are measured by the bench, not
-    asserted here."""
+    surrogate warm start (its first Fourier step corrected by the surrogate
+    for the temperatures it leads to, the plain iteration after it) both
+    converge (no subcell temperature changes by more than max(0.1 K, the
+    Monte Carlo noise)), and the plain Monte Carlo judge finds the same peak
+    rise at both results (within 3% or 3 standard errors).  What the network
+    gains: the warm start's first iterate is closer to the converged peak
+    than the plain loop's, and it needs no more Monte Carlo iterations."""
     from paper_1707_09073_gb300 import electrothermal as ET
     from paper_1707_09073_gb300 import surrogate as S
     base = W.bulk()
@@ -64,14 +66,41 @@ def test_electrothermal_warm_start(emc):
     sur.fit(X, Y, steps=3000, batch=1024, lr=2e-3, seed=6)
     cfgs = [W.nanowire(n_particles=40_000, nx=20, Lx=200e-9, Vd=float(v), seed=50 + v) for v in (2, 4)]
     tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=1e9, L_boundary=120e-9, tol_K=1e-3)
-    with emc.Context(cfgs) as ctx:
-        ET.warm_to_steady(ctx)
-        plain = ET.iterate(ctx, tc, np.full((2, ctx.n_cell), 300.0), max_iter=12, rtol=0.01)
-    with emc.Context(cfgs) as ctx:
-        ET.warm_to_steady(ctx)
-        warm = ET.surrogate_accelerated(ctx, sur, tc, np.full((2, ctx.n_cell), 300.0), max_iter=12, rtol=0.01)
-    assert plain["converged"] and warm["converged"], (plain["history"], warm["history"])
-    assert warm["iterations"] <= plain["iterations"] + 2, (plain["history"], warm["history"])
-    assert np.all(np.abs(warm["peak"] - plain["peak"]) <= np.maximum(0.03 * plain["peak"], 0.5)), \
-        (warm["peak"], plain["peak"])
-    assert (plain["peak"] > 1.0).all()
+    res = {}
+    for mode in ("plain", "warm"):
+        with emc.Context(cfgs) as ctx:
+            ET.warm_to_steady(ctx)
+            T0 = np.full((2, ctx.n_cell), 300.0)
+            r = (ET.iterate(ctx, tc, T0, max_iter=12) if mode == "plain"
+                 else ET.surrogate_accelerated(ctx, sur, tc, T0, max_iter=12, corrected_iters=1))
+            res[mode] = (r, ET.judge(ctx, tc, r["T"], avg_steps=3000))
+    (rp, jp), (rs, js) = res["plain"], res["warm"]
+    assert rp["converged"] and rs["converged"], (rp["history"], rs["history"])
+    assert (jp["peak"] > 1.0).all()
+    se = np.hypot(jp["peak_se"], js["peak_se"])
+    assert np.all(np.abs(js["peak"] - jp["peak"]) <= np.maximum(0.03 * jp["peak"], 3 * se)), (js["peak"], jp["peak"], se)
+    first_p = np.abs(rp["history"][0] - jp["peak"]) / jp["peak"]
+    first_s = np.abs(rs["history"][0] - jp["peak"]) / jp["peak"]
+    assert first_s.max() < first_p.max(), (first_s, first_p)
+    assert rs["iterations"] <= rp["iterations"], (rp["iterations"], rs["iterations"])
+
+
+def test_thermal_solve_with_interface_of_eqs_2_and_3(emc):
+    """The Fourier solve with the diffuse-mismatch GaN/SiC interface (Eqs.
+    (2)-(3), 1/R_K at the bottom subcells' temperatures) under the bottom
+    face, alone and in series with a lumped conductance, against the
+    reference solve (1e-5)."""
+    from oracle import thermal as tref
+    cfg = W.nanowire(n_particles=10, nx=20, Lx=200e-9, Vd=1.0, seed=4)
+    C = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    rng = np.random.default_rng(3)
+    q = (np.abs(rng.normal(size=(1, C))) * 3e17 + 1e17)
+    for ratio, hb in ((1.0, 0.0), (10.0, 5e8)):
+        tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=hb, L_boundary=120e-9, tol_K=1e-9,
+                                    substrate=W.TABLE_II_SIC, area_ratio=ratio)
+        with emc.Context(cfg) as ctx:
+            T, _ = emc.emc.thermal_solve(ctx, tc, q)
+        want = tref.solve(cfg, q[0], W.TABLE_II_GAN, h_bottom=hb, L_b=120e-9, tol=1e-9, substrate=W.TABLE_II_SIC,
+                          area_ratio=ratio)
+        np.testing.assert_allclose(T[0] - 300.0, want - 300.0, rtol=1e-5)
+        assert (T[0] > 300.0).all()

@@ -110,3 +110,80 @@ def test_electron_scattering_kappa_reduction():
     k1 = thermal.kappa(300.0, W.TABLE_II_GAN, n_e=1e24, elec=el)
     assert k7 < k1 < k0
     assert thermal.kappa(300.0, W.TABLE_II_GAN, n_e=0.0, elec=el) == k0
+
+
+# ---------------------------------------- diffuse mismatch model, Eqs. (2)-(3)
+KB, HB = 1.380649e-23, 1.054571817e-34
+
+
+def sound_speed(mat):
+    """Long-wavelength group velocity of the sine branch, omega_max pi / 2 q0."""
+    return mat["omega_max_rad_s"] * np.pi / (2.0 * mat["k0_per_m"])
+
+
+def test_dmm_transmissivities_are_complementary_and_reciprocal():
+    """tau_12 + tau_21 = 1 where both sides have states, the detailed balance
+    of the diffuse mismatch model (sum v D)_1 tau_12 = (sum v D)_2 tau_21,
+    one half between identical materials, and nothing transmitted into
+    material 2 above its highest frequency."""
+    gan, sic = W.TABLE_II_GAN, W.TABLE_II_SIC
+    for w in np.linspace(1e11, 0.999 * gan["omega_max_rad_s"], 23):
+        t12, t21 = thermal.tau12(w, gan, sic), thermal.tau12(w, sic, gan)
+        assert t12 + t21 == pytest.approx(1.0, abs=1e-14)
+        _, v1, D1 = thermal.branch(gan, w)
+        _, v2, D2 = thermal.branch(sic, w)
+        assert v1 * D1 * t12 == pytest.approx(v2 * D2 * t21, rel=1e-12)
+        assert thermal.tau12(w, gan, gan) == pytest.approx(0.5, abs=1e-15)
+    for w in np.linspace(1.001 * gan["omega_max_rad_s"], 0.999 * sic["omega_max_rad_s"], 7):
+        assert thermal.tau12(w, sic, gan) == 0.0
+        assert thermal.tau12(w, gan, sic) == 1.0  # Eq. (2) with no states on the wire's side
+    # long waves: tau_12 -> v_1^2 / (v_1^2 + v_2^2) (linear dispersion)
+    v1, v2 = sound_speed(gan), sound_speed(sic)
+    assert thermal.tau12(1e9, gan, sic) == pytest.approx(v1 ** 2 / (v1 ** 2 + v2 ** 2), rel=1e-6)
+
+
+def test_interface_conductance_low_temperature_limit():
+    """Only long waves are excited at low T: Eq. (3) becomes
+    1/R_K = pi^2 k^4 T^3 tau_12(0) / (10 hbar^3 v_1^2) (three branches,
+    integral of x^4 e^x / (e^x - 1)^2 = 4 pi^4 / 15)."""
+    gan, sic = W.TABLE_II_GAN, W.TABLE_II_SIC
+    v1, v2 = sound_speed(gan), sound_speed(sic)
+    t0 = v1 ** 2 / (v1 ** 2 + v2 ** 2)
+    for T in (0.05, 0.1):
+        want = np.pi ** 2 * KB ** 4 * T ** 3 * t0 / (10.0 * HB ** 3 * v1 ** 2)
+        assert thermal.interface_conductance(T, gan, sic) == pytest.approx(want, rel=1e-5)
+
+
+def test_interface_conductance_classical_limit():
+    """At high T every mode holds k: between identical materials (tau = 1/2)
+    Eq. (3) becomes (3/8) (k / 2 pi^2) (2 q0 / pi)^2 omega_max (pi^2/4 - 2),
+    the integral of arcsin^2 over [0, 1] being pi^2/4 - 2."""
+    gan = W.TABLE_II_GAN
+    q0, wm = gan["k0_per_m"], gan["omega_max_rad_s"]
+    want = 3.0 / 8.0 * KB / (2 * np.pi ** 2) * (2 * q0 / np.pi) ** 2 * wm * (np.pi ** 2 / 4 - 2)
+    assert thermal.interface_conductance(1e7, gan, gan) == pytest.approx(want, rel=1e-8)
+
+
+def test_interface_conductance_gan_on_sic():
+    """GaN -> SiC at 300 K: R_K = 2.32e-8 m^2 K/W from Eqs. (2)-(3) with the
+    Table II dispersions (context: measured GaN/SiC boundary resistances are
+    of order 1e-8); it saturates with temperature as the modes fill."""
+    g300 = thermal.interface_conductance(300.0, W.TABLE_II_GAN, W.TABLE_II_SIC)
+    assert 1.0 / g300 == pytest.approx(2.32e-8, rel=0.01)
+    g600 = thermal.interface_conductance(600.0, W.TABLE_II_GAN, W.TABLE_II_SIC)
+    g50 = thermal.interface_conductance(50.0, W.TABLE_II_GAN, W.TABLE_II_SIC)
+    assert g50 < g300 < g600 < 1.01 * thermal.interface_conductance(1e5, W.TABLE_II_GAN, W.TABLE_II_SIC)
+
+
+def test_fourier_bottom_boundary_puts_the_interface_in_series():
+    """The operator's bottom boundary with an interface conductance G per
+    area equals the lumped boundary with 1/h = 1/h_lumped + 1/G (the half
+    cell, the lumped part and the interface in series)."""
+    cfg = grid(6)
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    kap = np.full(n, 100.0)
+    g_if = np.full(n, 4.0e7)
+    A1, b1 = thermal.operator(cfg, kap, 300.0, 5e8, g_if)
+    A2, b2 = thermal.operator(cfg, kap, 300.0, 1.0 / (1.0 / 5e8 + 1.0 / 4.0e7))
+    np.testing.assert_allclose(A1.toarray(), A2.toarray(), rtol=1e-13)
+    np.testing.assert_allclose(b1, b2, rtol=1e-13)

@@ -318,6 +318,14 @@ def electrothermal_comparison(args, stream) -> dict:
             ctx.close()
     plain = out["plain"]["_judge"]
     hot = plain["peak"] >= 5.0
+    # accuracy per Monte Carlo run: the first iteration whose peak rise at the
+    # highest bias is within 2% / 1% of the judged plain fixed point
+    ref_pk = float(plain["peak"][-1])
+    for m in out:
+        h = [float(x[-1]) for x in out[m]["_r"]["history"]]
+        for tol in (0.02, 0.01):
+            it = next((i + 1 for i, x in enumerate(h) if abs(x - ref_pk) <= tol * ref_pk), None)
+            out[m]["mc_runs_to_within_%dpct_of_judged_peak" % round(100 * tol)] = it
     cmp = {}
     for mode in ("surrogate_warm_start", "surrogate", "surrogate_heat_start"):
         jm = out[mode]["_judge"]

@@ -89,6 +89,19 @@ typedef struct emc_config {
     double p_specular;      /* specular fraction on the outer side/top/bottom walls */
     int64_t n_particles;    /* initial electrons (superparticles) */
     int64_t capacity;       /* particle slots (>= n_particles; spare slots for injection) */
+    /* Particle sharding of one wire over several contexts (usually one per
+     * GPU; see emc_shard_counts).  All three zero: unsharded.  A wire of N
+     * initial electrons and S spare slots has global particle ids [0, N)
+     * (initial electrons) and [N, N + S) (spare slots), as an unsharded
+     * context numbers them.  A shard holds the global ids
+     * [shard_live_base, shard_live_base + n_particles) and
+     * [shard_spare_base, shard_spare_base + capacity - n_particles).  The
+     * global id keys the particle's Philox stream, so every particle draws
+     * the same numbers however the wire is split. */
+    int64_t shard_n_global;   /* N, > 0 in a sharded context (the superparticle weight
+                                 Nd V / N and the contact refill target use it) */
+    int64_t shard_live_base;  /* global id of this shard's first initial electron */
+    int64_t shard_spare_base; /* global id of this shard's first spare slot (>= N) */
     int32_t Z[3];           /* valley degeneracies */
     int32_t geometry;       /* EMC_GEOM_BULK or EMC_GEOM_NANOWIRE */
     int32_t n_bins;         /* rate-table bins (table spans [0, n_bins * dE_eV)) */
@@ -243,6 +256,49 @@ emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null,
 emc_status emc_state_size(emc_ctx* ctx, size_t* bytes);
 emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes);
 emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes);
+
+/* One wire's particles sharded over several contexts (the charge exchange
+ * of the Poisson passage: the field of a period follows from the electron
+ * count of every subcell, summed over all particles of the wire).  Each
+ * context holds a disjoint set of the wire's particle ids (emc_config
+ * shard_*; every ensemble of a sharded context is sharded, and a context is
+ * either all sharded or not).  Within a Poisson period the shards advance
+ * independently; at its end the caller sums the per-subcell counts over the
+ * shards (an integer all-reduce) and hands the sum back, and every shard
+ * refills the contacts and solves the same FP64 Poisson problem, so all
+ * shards hold the same field.  The union of the shards then follows, bit for
+ * bit, the run of one unsharded context of the whole wire: the same particle
+ * states, integer tallies summed over the shards equal to its tallies.
+ *
+ * Protocol per shard:
+ *   - after emc_init, and after every emc_step that ends a Poisson period,
+ *     the context waits for an exchange (emc_step in that state, and
+ *     emc_step across the end of a period, are EMC_EINVAL; so are
+ *     emc_set_bias(_all), emc_get_state and emc_set_state);
+ *   - emc_shard_counts copies the shard's electron count per subcell
+ *     (int32[E][C], counted at the end of the period) into charge_out and
+ *     its free-id counts into free_out (int64[E][2]: free ids among the
+ *     initial-electron ids, and among the spare ids);
+ *   - the caller sums charge over the shards (charge_global) and, for each
+ *     shard, the free counts of the shards whose id ranges lie below it
+ *     (free_prefix[E][2]) and over all shards (free_total[E][2]); shards are
+ *     ordered by shard_live_base, whose order must be that of
+ *     shard_spare_base;
+ *   - emc_shard_tail hands these back: the contact subcells are refilled
+ *     with the r-th free id of the whole wire filling the r-th missing
+ *     electron (each shard draws the electrons of the free ids it holds),
+ *     the charge becomes the wire's count after the refill, and the FP64
+ *     Poisson update recomputes the field (after emc_init: no refill, the
+ *     initial solve).  lead = 1 on exactly one shard: its count of refills
+ *     skipped for lack of free ids is the wire's.
+ * Pointers may be host or device memory (copies are in stream order; both
+ * calls synchronise the context stream).  Tallies of a shard are its own
+ * particles' (sum them over the shards), except EMC_TALLY_CHARGE, PHI and
+ * FIELD, which are the wire's on every shard.  Errors: EMC_EINVAL when no
+ * exchange is pending or the context is not sharded. */
+emc_status emc_shard_counts(emc_ctx* ctx, int32_t* charge_out, int64_t* free_out);
+emc_status emc_shard_tail(emc_ctx* ctx, const int32_t* charge_global, const int64_t* free_prefix,
+                          const int64_t* free_total, int32_t lead);
 
 /* Lattice temperature per subcell of ensemble ens (nanowire contexts whose
  * ensembles share one material and doping): T_cells[n] in K, n = the

@@ -55,7 +55,7 @@ struct DevParams {
     void *kx, *ky, *kz, *x, *y, *z, *tr;
     uint32_t* tag;  // (ensemble << 8) | valley, valley DEAD = no particle
     uint64_t* ctr;  // Philox counter of the particle's stream
-    uint32_t* id;   // particle id within its ensemble (Philox key word 1)
+    uint32_t* id;   // particle id within its ensemble's slots (local id)
     int64_t n_slots;
     // per ensemble
     int32_t n_ens;
@@ -67,6 +67,14 @@ struct DevParams {
     const void* acc_bulk;     // Real[E][4]: dk/dt under the uniform field, 1/(nm fs); 4th unused
     const void* acc_cell;     // Real[E][C][4]: dk/dt per subcell and 1/(hbar |dk/dt|)
     const int32_t* n_target;  // contact-cell refill target per ensemble
+    // global particle ids (the Philox key word 1): local id i < n0 is global
+    // id gid[e][0] + i, a spare local id i >= n0 is gid[e][1] + i - n0
+    // (unsharded: {0, n0}, the global id is the local id)
+    const uint32_t* ens_gid;  // [E][2]
+    // sharded contexts: per ensemble {free ids of the lower shards among the
+    // initial-electron ids, among the spare ids, the wire's free initial-
+    // electron ids, the wire's free spare ids, lead shard}; null: unsharded
+    const long long* shard;   // [E][5]
     uint32_t* slot_of_id;     // [total slots] global slot of (ensemble, id)
     uint32_t* dead_bits;      // per-ensemble bitmaps of free ids
     const int64_t* bits_off;  // word offset of ensemble e's bitmap

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <map>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -20,6 +21,7 @@ namespace emc {
 template <typename Real> void launch_flight(const DevParams&, bool, int, int, int, int, cudaStream_t);
 template <typename Real> void launch_init(const DevParams&, bool, cudaStream_t);
 template <typename Real> void launch_inject(const DevParams&, cudaStream_t);
+template <typename Real> void launch_free_counts(const DevParams&, long long*, cudaStream_t);
 template <typename Real> cudaError_t flight_set_smem(size_t);
 template <typename Real> size_t flight_smem_bytes(int, int);
 template <typename Real> int flight_blocks_per_sm(bool, int, size_t);
@@ -74,6 +76,10 @@ struct emc_ctx {
     int nx = 1, ny = 1, nz = 1, ncell = 1, nb = 0, n_tab = 0, block = 256, spl = 50, K = 10, grid_cap = 1;
     int sort_period = 0;
     int64_t n_slots = 0, steps_done = 0, launches = 0, bits_words = 0;
+    // particle sharding: 0 no exchange pending, 1 the initial solve, 2 the
+    // refill and Poisson update at the end of a period
+    bool sharded = false;
+    int shard_pending = 0;
     double dt_fs = 1.0, dE = 0.002;
     double Lx = 1, Ly = 1, Lz = 1, dx = 1, dy = 1, dz = 1;  // nm
     std::vector<int64_t> off, cap, n0;
@@ -92,6 +98,8 @@ struct emc_ctx {
     int64_t *d_off = nullptr, *d_cap = nullptr, *d_n0 = nullptr, *d_bits_off = nullptr;
     uint32_t* d_seed = nullptr;
     int32_t *d_tabset = nullptr, *d_target = nullptr;
+    uint32_t* d_gid = nullptr;
+    long long *d_shard = nullptr, *d_free = nullptr;
     void *acc_bulk = nullptr, *acc_cell = nullptr, *table = nullptr, *phys = nullptr;
     double* tab64 = nullptr;
     unsigned long long *events = nullptr, *cnt = nullptr;
@@ -565,6 +573,17 @@ emc_status validate(const emc_config* c, int n, emc_ctx* ctx)
         if (b.table_smem_kb < 0 || b.table_smem_kb > 200) return fail(ctx, EMC_EINVAL, "table_smem_kb in [0, 200]");
         if (b.steps_per_launch > 1000 || b.steps_per_poisson > 1000)
             return fail(ctx, EMC_EINVAL, "steps_per_launch and steps_per_poisson at most 1000");
+        const bool sh = b.shard_n_global != 0 || b.shard_live_base != 0 || b.shard_spare_base != 0;
+        if (sh != (a.shard_n_global != 0 || a.shard_live_base != 0 || a.shard_spare_base != 0))
+            return fail(ctx, EMC_EINVAL, "shards: every ensemble of a context sharded, or none");
+        if (sh) {
+            const int64_t spare = std::max<int64_t>(b.capacity, b.n_particles) - b.n_particles;
+            if (b.geometry != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_EINVAL, "shards: nanowire only");
+            if (b.shard_n_global <= 0 || b.shard_live_base < 0 || b.shard_live_base + b.n_particles > b.shard_n_global ||
+                b.shard_spare_base < b.shard_n_global || b.shard_spare_base + spare > 0xFFFFFFFFll)
+                return fail(ctx, EMC_EINVAL, "shards: need 0 <= live_base, live_base + n_particles <= N, "
+                                             "N <= spare_base, spare_base + spare slots <= 2^32");
+        }
     }
     return EMC_OK;
 }
@@ -729,6 +748,8 @@ void fill_params(emc_ctx* ctx)
     P.seed = ctx->d_seed; P.tabset = ctx->d_tabset;
     P.acc_bulk = ctx->acc_bulk; P.acc_cell = ctx->acc_cell;
     P.n_target = ctx->d_target;
+    P.ens_gid = ctx->d_gid;
+    P.shard = ctx->d_shard;
     P.slot_of_id = ctx->slot_of_id; P.dead_bits = ctx->dead_bits; P.bits_off = ctx->d_bits_off;
     P.table = ctx->table; P.phys = ctx->phys;
     P.n_tab = ctx->n_tab; P.nb = ctx->nb;
@@ -1129,7 +1150,8 @@ emc_status init_impl(emc_ctx* ctx)
         CK(cudaMemsetAsync(ctx->charge, 0, sizeof(int) * (size_t)ctx->n_ens * ctx->ncell, ctx->st));
         launch_flight<Real>(ctx->P, true, 0, 1, ctx->block, ctx->grid_cap, ctx->st);
         ctx->launches += 1;
-        if ((s = poisson_update<Real>(ctx)) != EMC_OK) return s;
+        if (ctx->sharded) ctx->shard_pending = 1;  // the wire's count first (emc_shard_tail)
+        else if ((s = poisson_update<Real>(ctx)) != EMC_OK) return s;
     }
     CK(cudaGetLastError());
     return check_err(ctx);
@@ -1190,6 +1212,9 @@ emc_status step_impl(emc_ctx* ctx, int32_t n)
             const int into = int(ctx->steps_done % ctx->K);
             chunk = std::min(n, ctx->K - into);
             boundary = (into + chunk == ctx->K);
+            if (ctx->sharded && (ctx->shard_pending || n > ctx->K - into))
+                return fail(ctx, EMC_EINVAL, ctx->shard_pending ? "shards: exchange pending (emc_shard_tail)"
+                                                                : "shards: emc_step may not cross the end of a Poisson period");
             if (boundary)
                 CK(cudaMemsetAsync(ctx->charge, 0, sizeof(int) * (size_t)ctx->n_ens * ctx->ncell, ctx->st));
         } else {
@@ -1204,6 +1229,14 @@ emc_status step_impl(emc_ctx* ctx, int32_t n)
         launch_flight<Real>(ctx->P, nw, chunk, boundary ? 1 : 0, ctx->block, ctx->grid_cap, ctx->st);
         ctx->launches += 1;
         if (ctx->prof) CK(cudaEventRecord(e1, ctx->st));
+        if (boundary && ctx->sharded) {
+            // refill and Poisson update wait for the wire's count
+            ctx->shard_pending = 2;
+            ctx->steps_done += chunk;
+            if (ctx->sort_period > 0) ++ctx->flights_since_sort;
+            CK(cudaGetLastError());
+            return EMC_OK;
+        }
         if (boundary) {
             emc_status s = chunk_tail<Real>(ctx);
             if (s != EMC_OK) return s;
@@ -1216,6 +1249,23 @@ emc_status step_impl(emc_ctx* ctx, int32_t n)
             if (s != EMC_OK) return s;
             ctx->flights_since_sort = 0;
         }
+    }
+    return EMC_OK;
+}
+
+template <typename Real>
+emc_status shard_tail_impl(emc_ctx* ctx)
+{
+    if (ctx->shard_pending == 1) {
+        ctx->shard_pending = 0;
+        return poisson_update<Real>(ctx);
+    }
+    ctx->shard_pending = 0;
+    emc_status s = chunk_tail<Real>(ctx);
+    if (s != EMC_OK) return s;
+    if (ctx->sort_period > 0 && ctx->flights_since_sort >= ctx->sort_period) {
+        if ((s = sort_particles<Real>(ctx)) != EMC_OK) return s;
+        ctx->flights_since_sort = 0;
     }
     return EMC_OK;
 }
@@ -1271,6 +1321,8 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
     std::vector<int64_t> bits_off(n_ens);
     std::vector<uint32_t> seeds(n_ens);
     std::vector<int32_t> target(n_ens);
+    std::vector<uint32_t> gid((size_t)2 * n_ens);
+    ctx->sharded = cfgs[0].shard_n_global > 0;
     int64_t o = 0, bo = 0;
     for (int e = 0; e < n_ens; ++e) {
         const emc_config& c = cfgs[e];
@@ -1290,7 +1342,11 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
         }
         ctx->tabset[e] = ts;
         const double V = c.Lx * c.Ly * c.Lz;
-        ctx->w[e] = (ctx->geom == EMC_GEOM_NANOWIRE && c.n_particles > 0) ? c.Nd_m3 * V / (double)c.n_particles : 1.0;
+        // the wire's initial electrons (all shards) set the superparticle weight
+        const int64_t n_wire = ctx->sharded ? c.shard_n_global : c.n_particles;
+        gid[2 * e] = ctx->sharded ? uint32_t(c.shard_live_base) : 0u;
+        gid[2 * e + 1] = ctx->sharded ? uint32_t(c.shard_spare_base) : uint32_t(c.n_particles);
+        ctx->w[e] = (ctx->geom == EMC_GEOM_NANOWIRE && n_wire > 0) ? c.Nd_m3 * V / (double)n_wire : 1.0;
         const double Vcell = V / ctx->ncell;
         target[e] = (ctx->geom == EMC_GEOM_NANOWIRE) ? (int32_t)std::llround(c.Nd_m3 * Vcell / ctx->w[e]) : 0;
         ctx->bias[3 * e] = c.Vs;
@@ -1318,6 +1374,11 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
     CKI(dalloc(ctx, &ctx->d_seed, n_ens));
     CKI(dalloc(ctx, &ctx->d_tabset, n_ens));
     CKI(dalloc(ctx, &ctx->d_target, n_ens));
+    CKI(dalloc(ctx, &ctx->d_gid, (size_t)2 * n_ens));
+    if (ctx->sharded) {
+        CKI(dalloc(ctx, &ctx->d_shard, (size_t)5 * n_ens));
+        CKI(dalloc(ctx, &ctx->d_free, (size_t)2 * n_ens));
+    }
     CKI(dalloc(ctx, &ctx->events, (size_t)n_ens * ctx->ncell * NV * NM));
     CKI(dalloc(ctx, &ctx->cnt, (size_t)n_ens * NCNT));
     CKI(dalloc(ctx, &ctx->sums, (size_t)n_ens * NSUM));
@@ -1334,6 +1395,7 @@ emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, e
     CKI(up(ctx->d_seed, seeds.data(), 4 * n_ens));
     CKI(up(ctx->d_tabset, ctx->tabset.data(), 4 * n_ens));
     CKI(up(ctx->d_target, target.data(), 4 * n_ens));
+    CKI(up(ctx->d_gid, gid.data(), 8 * n_ens));
     CKI(up(ctx->alive, ctx->n0.data(), 8 * n_ens));
 #undef CKI
     if (ctx->prec == EMC_FP64) return init_impl<double>(ctx);
@@ -1605,10 +1667,12 @@ static_assert(sizeof(StateHeader) == 72, "the state header layout is part of the
 uint64_t cfg_hash(const emc_ctx* ctx)
 {
     uint64_t h = 1469598103934665603ull;
+    // the fields up to the last one (trailing padding bytes are not hashed)
+    const size_t used = offsetof(emc_config, table_smem_kb) + sizeof(int32_t);
     for (emc_config c : ctx->cfg) {
         c.sort_period = c.block_size = c.steps_per_launch = c.table_smem_kb = 0;
         const unsigned char* b = reinterpret_cast<const unsigned char*>(&c);
-        for (size_t i = 0; i < sizeof c; ++i) h = (h ^ b[i]) * 1099511628211ull;
+        for (size_t i = 0; i < used; ++i) h = (h ^ b[i]) * 1099511628211ull;
     }
     return h;
 }
@@ -1660,6 +1724,7 @@ emc_status emc_state_size(emc_ctx* ctx, size_t* bytes)
 emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes)
 {
     if (!ctx || !dst) return EMC_EINVAL;
+    if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     const bool tmode = ctx->cell_bin != nullptr;
     if (bytes < state_bytes(ctx, tmode)) return fail(ctx, EMC_EINVAL, "emc_get_state: destination too small");
     StateHeader h{};
@@ -1690,6 +1755,7 @@ emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes)
 emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes)
 {
     if (!ctx || !src) return EMC_EINVAL;
+    if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     if (bytes < sizeof(StateHeader)) return fail(ctx, EMC_EINVAL, "emc_set_state: blob too small");
     StateHeader h;
     std::memcpy(&h, src, sizeof h);
@@ -1731,6 +1797,7 @@ emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes)
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg)
 {
     if (!ctx || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
+    if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     if (!std::isfinite(Vs) || !std::isfinite(Vd) || !std::isfinite(Vg))
         return fail(ctx, EMC_EINVAL, "emc_set_bias: terminal voltages must be finite");
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias needs the nanowire geometry");
@@ -1751,6 +1818,7 @@ emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double 
 emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias)
 {
     if (!ctx || !bias) return EMC_EINVAL;
+    if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias_all needs the nanowire geometry");
     for (int i = 0; i < 3 * ctx->n_ens; ++i)
         if (!std::isfinite(bias[i])) return fail(ctx, EMC_EINVAL, "emc_set_bias_all: terminal voltages must be finite");
@@ -1819,6 +1887,51 @@ emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_lau
     if (flight_ms) *flight_ms = tot;
     if (flight_launches) *flight_launches = (int64_t)(ctx->ev_used / 2);
     return EMC_OK;
+}
+
+emc_status emc_shard_counts(emc_ctx* ctx, int32_t* charge_out, int64_t* free_out)
+{
+    if (!ctx || !charge_out || !free_out) return EMC_EINVAL;
+    if (!ctx->sharded || !ctx->shard_pending)
+        return fail(ctx, EMC_EINVAL, "emc_shard_counts: no exchange pending (or not a sharded context)");
+    launch_free_counts<float>(ctx->P, ctx->d_free, ctx->st);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    const size_t nc = (size_t)ctx->n_ens * ctx->ncell;
+    CK(cudaMemcpyAsync(charge_out, ctx->charge, sizeof(int) * nc, cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(free_out, ctx->d_free, sizeof(long long) * 2 * ctx->n_ens, cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return check_err(ctx);
+}
+
+emc_status emc_shard_tail(emc_ctx* ctx, const int32_t* charge_global, const int64_t* free_prefix,
+                          const int64_t* free_total, int32_t lead)
+{
+    if (!ctx || !charge_global || !free_prefix || !free_total) return EMC_EINVAL;
+    if (!ctx->sharded || !ctx->shard_pending)
+        return fail(ctx, EMC_EINVAL, "emc_shard_tail: no exchange pending (or not a sharded context)");
+    const int E = ctx->n_ens;
+    // host copies of the small per-ensemble inputs (they may be device memory)
+    std::vector<long long> pre((size_t)2 * E), tot((size_t)2 * E), sh((size_t)5 * E);
+    CK(cudaMemcpyAsync(pre.data(), free_prefix, sizeof(long long) * 2 * E, cudaMemcpyDefault, ctx->st));
+    CK(cudaMemcpyAsync(tot.data(), free_total, sizeof(long long) * 2 * E, cudaMemcpyDefault, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int e = 0; e < E; ++e) {
+        if (pre[2 * e] < 0 || pre[2 * e + 1] < 0 || tot[2 * e] < pre[2 * e] || tot[2 * e + 1] < pre[2 * e + 1])
+            return fail(ctx, EMC_EINVAL, "emc_shard_tail: need 0 <= free_prefix <= free_total");
+        sh[5 * e] = pre[2 * e];
+        sh[5 * e + 1] = pre[2 * e + 1];
+        sh[5 * e + 2] = tot[2 * e];
+        sh[5 * e + 3] = tot[2 * e + 1];
+        sh[5 * e + 4] = lead ? 1 : 0;
+    }
+    CK(cudaMemcpyAsync(ctx->d_shard, sh.data(), sizeof(long long) * 5 * E, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->charge, charge_global, sizeof(int) * (size_t)E * ctx->ncell, cudaMemcpyDefault,
+                       ctx->st));
+    emc_status s = ctx->prec == EMC_FP64 ? shard_tail_impl<double>(ctx) : shard_tail_impl<float>(ctx);
+    if (s != EMC_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    return check_err(ctx);
 }
 
 emc_status emc_set_temperature(emc_ctx* ctx, int32_t ens, const double* T_cells, int32_t n)

@@ -6,6 +6,7 @@ template void launch_flight<float>(const DevParams&, bool, int, int, int, int, c
 template void launch_init<float>(const DevParams&, bool, cudaStream_t);
 template void launch_rescale<float>(const DevParams&, int, int64_t, const double*, cudaStream_t);
 template void launch_inject<float>(const DevParams&, cudaStream_t);
+template void launch_free_counts<float>(const DevParams&, long long*, cudaStream_t);
 template cudaError_t flight_set_smem<float>(size_t);
 template size_t flight_smem_bytes<float>(int, int);
 template int flight_blocks_per_sm<float>(bool, int, size_t);

@@ -168,6 +168,13 @@ struct Part {
     }
 };
 
+// global id (Philox key word 1) of local id i of ensemble e
+__device__ __forceinline__ uint32_t gid_of(const DevParams& P, int e, uint32_t i)
+{
+    const uint32_t n0 = uint32_t(P.ens_n0[e]);
+    return i < n0 ? P.ens_gid[2 * e] + i : P.ens_gid[2 * e + 1] + (i - n0);
+}
+
 template <typename Real>
 __device__ __forceinline__ int cell_of(const KConst<Real>& K, Real x, Real y, Real z)
 {
@@ -326,8 +333,7 @@ __device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, const K
     else if (q.x > K.Lx) out = CNT_DRN_OUT;
     if (out >= 0) {
         tally_cnt(bt, P, q.e, e_base, out, 1u);
-        atomicOr(&P.dead_bits[P.bits_off[q.e] + (q.id >> 5)], 1u << (q.id & 31u));
-        return true;
+        return true;  // the caller frees the id
     }
     if (q.y < Real(0)) {
         q.y = -q.y;
@@ -736,7 +742,7 @@ __global__ void __launch_bounds__(256, 4)
         }
         q.tr = static_cast<const Real*>(P.tr)[p];
         q.ctr = P.ctr[p];
-        q.id = P.id[p];
+        q.id = gid_of(P, q.e, P.id[p]);
         q.seed = P.seed[q.e];
         const int ts = P.tabset[q.e];
         const Phys<Real>& ph = (ts < K.n_tab_s) ? ph_s[ts] : ph_g[ts];
@@ -785,6 +791,11 @@ __global__ void __launch_bounds__(256, 4)
         ss.fold(S);
         store<Real>(P, p, q, NW);
         P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
+        if (NW && !live) {
+            // left through a contact: its id is free for the refill
+            const uint32_t i = P.id[p];
+            atomicOr(&P.dead_bits[P.bits_off[q.e] + (i >> 5)], 1u << (i & 31u));
+        }
         if (NW && count_charge && live) agg_add_i(P.charge, q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z));
     }
     S.flush_warp(P, bt, e_base, true);
@@ -810,7 +821,7 @@ __global__ void k_init(const DevParams P)
     P.slot_of_id[s] = uint32_t(s);
     Part<Real> q;
     q.e = e;
-    q.id = id;
+    q.id = gid_of(P, e, id);
     q.seed = P.seed[e];
     q.ctr = 0;
     if ((int64_t)id < P.ens_n0[e]) {
@@ -830,24 +841,43 @@ __global__ void k_init(const DevParams P)
 
 // --------------------------------------------------------------- inject
 // Refill each contact subcell (the x = 0 layer first, then x = Lx, cells in
-// (y, z) order) up to n_target electrons, taking free ids of the ensemble in
-// increasing order: the r-th free id fills the r-th missing electron.  One
-// block per ensemble.  Threads own contiguous words of the free-id bitmap;
-// a block scan of the words' population counts gives each free id its rank,
-// ids are gathered by rank into shared memory (INJ per round) and the new
-// electrons are drawn in parallel.  Dynamic shared memory: the deficit prefix
-// sums (2 ny nz + 1 ints), a scan buffer (blockDim ints) and INJ ids.
+// (y, z) order) up to n_target electrons, taking free ids of the wire in
+// increasing global order: the r-th free id fills the r-th missing electron.
+// The global order ranks the free initial-electron ids (global ids < N) of
+// all shards first, shard by shard, then the free spare ids, shard by shard;
+// unsharded, it is the order of the local ids.  One block per ensemble.
+// Threads own contiguous words of the free-id bitmap; a block scan of the
+// words' population counts (initial-electron and spare ids apart) gives
+// each free id its rank, ids are gathered by rank into shared memory (INJ
+// per round) and the new electrons are drawn in parallel.  The subcell
+// charge grows by the wire's refill of each contact subcell, which the
+// deficits and the wire's free-id count fix, so every shard ends with the
+// wire's count.  Dynamic shared memory: a scan buffer (blockDim 64-bit
+// words), the deficit prefix sums (2 ny nz + 1 ints) and INJ ids.
 constexpr int INJ = 1024;
+
+// free ids among local ids [32 w, 32 w + 32) below n0 (initial-electron
+// ids) and at or above it (spare ids)
+__device__ __forceinline__ void free_split(uint32_t word, int64_t w, int64_t n0, int& a, int& b)
+{
+    const int64_t lo = 32 * w;
+    uint32_t ma;
+    if (lo + 32 <= n0) ma = 0xFFFFFFFFu;
+    else if (lo >= n0) ma = 0u;
+    else ma = (1u << uint32_t(n0 - lo)) - 1u;
+    a = __popc(word & ma);
+    b = __popc(word & ~ma);
+}
 
 template <typename Real>
 __global__ void __launch_bounds__(256) k_inject(const DevParams P)
 {
-    extern __shared__ int shi[];
+    extern __shared__ long long shl[];
     const int e = blockIdx.x;
     const int nface = P.ny * P.nz, ncon = 2 * nface;
-    int* pre = shi;
-    int* scan = shi + ncon + 1;
-    uint32_t* ids = reinterpret_cast<uint32_t*>(scan + blockDim.x);
+    long long* scan = shl;
+    int* pre = reinterpret_cast<int*>(scan + blockDim.x);
+    uint32_t* ids = reinterpret_cast<uint32_t*>(pre + ncon + 1);
     __shared__ int n_src, n_drn;
     // deficits of the contact cells, loaded in parallel, then their prefix
     // sums (pre[t] = electrons missing in contacts 0 .. t-1)
@@ -867,45 +897,80 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
     __syncthreads();
     const int D = pre[ncon];
     if (D == 0) return;
+    const int64_t n0 = P.ens_n0[e];
     const int64_t words = (P.ens_cap[e] + 31) / 32;
     uint32_t* bits = P.dead_bits + P.bits_off[e];
     const int64_t per = (words + blockDim.x - 1) / blockDim.x;
     const int64_t w0 = (int64_t)threadIdx.x * per;
     const int64_t w1 = w0 + per < words ? w0 + per : words;
-    int mine = 0;
-    for (int64_t w = w0; w < w1; ++w) mine += __popc(bits[w]);
+    int mine_a = 0, mine_b = 0;
+    for (int64_t w = w0; w < w1; ++w) {
+        int a, b;
+        free_split(bits[w], w, n0, a, b);
+        mine_a += a;
+        mine_b += b;
+    }
+    const long long mine = ((long long)mine_a << 32) | (long long)mine_b;
     scan[threadIdx.x] = mine;
     __syncthreads();
     for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        const int x = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0;
+        const long long x = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0;
         __syncthreads();
         scan[threadIdx.x] += x;
         __syncthreads();
     }
-    const int total = scan[blockDim.x - 1];
-    const int base = scan[threadIdx.x] - mine;
-    const int Deff = D < total ? D : total;
-    if (threadIdx.x == 0 && total < D)
+    const long long last = scan[blockDim.x - 1], incl = scan[threadIdx.x];
+    const long long loc_a = last >> 32, loc_b = last & 0xFFFFFFFFll;
+    long long off_a = 0, off_b = 0, tot_a = loc_a, tot_b = loc_b;
+    bool lead = true;
+    if (P.shard) {
+        const long long* sh = P.shard + 5 * (size_t)e;
+        off_a = sh[0];
+        off_b = sh[1];
+        tot_a = sh[2];
+        tot_b = sh[3];
+        lead = sh[4] != 0;
+    }
+    const long long total = tot_a + tot_b;
+    const int Deff = D < total ? D : int(total);
+    if (threadIdx.x == 0 && lead && total < D)
         atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_STARVED], (unsigned long long)(D - total));
+    // wire ranks of this thread's first free initial-electron id and first
+    // free spare id; along the thread's words the ranks rise, and every
+    // spare rank is above every initial-electron rank
+    const long long base_a = off_a + (incl >> 32) - mine_a;
+    const long long base_b = tot_a + off_b + (incl & 0xFFFFFFFFll) - mine_b;
+    const long long own_a0 = off_a, own_a1 = off_a + loc_a;
+    const long long own_b0 = tot_a + off_b, own_b1 = tot_a + off_b + loc_b;
     const Phys<Real>* ph = static_cast<const Phys<Real>*>(P.phys) + P.tabset[e];
     const Real len3[3] = {Real(P.dx), Real(P.dy), Real(P.dz)};
     for (int r0 = 0; r0 < Deff; r0 += INJ) {
         const int r1 = min(Deff, r0 + INJ);
+        // (block-uniform) no id of this shard has a rank in [r0, r1)
+        if (!(own_a0 < r1 && r0 < own_a1) && !(own_b0 < r1 && r0 < own_b1)) continue;
         // gather the ids of ranks [r0, r1) by rank
-        int rank = base;
+        long long rank = base_a;
+        bool in_b = false;
         for (int64_t w = w0; w < w1 && rank < r1; ++w) {
             uint32_t word = bits[w];
             while (word && rank < r1) {
                 const int bit = __ffs(word) - 1;
                 word &= word - 1u;
-                if (rank >= r0) ids[rank - r0] = uint32_t(w * 32 + bit);
+                const int64_t i = w * 32 + bit;
+                if (i >= n0 && !in_b) {
+                    in_b = true;
+                    rank = base_b;
+                    if (rank >= r1) break;
+                }
+                if (rank >= r0) ids[rank - r0] = uint32_t(i);
                 ++rank;
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) {
-            const int rk = r0 + i;
-            const uint32_t id = ids[i];
+        for (int k = threadIdx.x; k < r1 - r0; k += blockDim.x) {
+            const long long rk = r0 + k;
+            if (!((rk >= own_a0 && rk < own_a1) || (rk >= own_b0 && rk < own_b1))) continue;
+            const uint32_t id = ids[k];
             int lo = 0, hi = ncon - 1;  // contact t with pre[t] <= rk < pre[t + 1]
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -918,7 +983,7 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
             const int64_t slot = P.slot_of_id[P.ens_off[e] + id];
             Part<Real> q;
             q.e = e;
-            q.id = id;
+            q.id = gid_of(P, e, id);
             q.seed = P.seed[e];
             q.ctr = P.ctr[slot];
             const Real lo3[3] = {Real(ix * P.dx), Real(iy * P.dy), Real(iz * P.dz)};
@@ -933,30 +998,81 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
             new_electron<Real, true>(q, pi, lo3, len3, P.err);
             store<Real>(P, slot, q, true);
             P.tag[slot] = uint32_t(e) << 8;
-            atomicAdd(&P.charge[(size_t)e * P.ncell + ix * nface + rem], 1);
             atomicAdd(side ? &n_drn : &n_src, 1);
         }
         __syncthreads();
+    }
+    // the wire's refill of each contact subcell: the missing electrons of
+    // contact t whose ranks are below Deff
+    for (int t = threadIdx.x; t < ncon; t += blockDim.x) {
+        int got = Deff - pre[t];
+        const int need = pre[t + 1] - pre[t];
+        got = got < 0 ? 0 : (got > need ? need : got);
+        if (got > 0) {
+            const int side = t / nface, rem = t - side * nface;
+            const int ix = side ? P.nx - 1 : 0;
+            P.charge[(size_t)e * P.ncell + ix * nface + rem] += got;
+        }
     }
     // clear the bits of the ids taken (ranks below Deff).  The whole
     // ensemble is one block, so every thread's scan of the bitmap above has
     // finished before any bit changes (several blocks per ensemble would
     // rank against a bitmap that others are already clearing)
-    int rank = base;
+    long long rank = base_a;
+    bool in_b = false;
     for (int64_t w = w0; w < w1 && rank < Deff; ++w) {
         uint32_t word = bits[w], clear = 0u;
         while (word && rank < Deff) {
             const int bit = __ffs(word) - 1;
             word &= word - 1u;
+            if (w * 32 + bit >= n0 && !in_b) {
+                in_b = true;
+                rank = base_b;
+                if (rank >= Deff) break;
+            }
             clear |= 1u << bit;
             ++rank;
         }
         bits[w] &= ~clear;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_SRC_IN], (unsigned long long)n_src);
         atomicAdd(&P.cnt[(size_t)e * NCNT + CNT_DRN_IN], (unsigned long long)n_drn);
         atomicAdd(reinterpret_cast<unsigned long long*>(&P.alive[e]), (unsigned long long)(n_src + n_drn));
+    }
+}
+
+// Free ids of each ensemble among its initial-electron ids and among its
+// spare ids (out[e][0], out[e][1]); one block per ensemble.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_free_counts(const DevParams P, long long* out)
+{
+    __shared__ long long ra[256], rb[256];
+    const int e = blockIdx.x;
+    const int64_t n0 = P.ens_n0[e];
+    const int64_t words = (P.ens_cap[e] + 31) / 32;
+    const uint32_t* bits = P.dead_bits + P.bits_off[e];
+    long long sa = 0, sb = 0;
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) {
+        int a, b;
+        free_split(bits[w], w, n0, a, b);
+        sa += a;
+        sb += b;
+    }
+    ra[threadIdx.x] = sa;
+    rb[threadIdx.x] = sb;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            ra[threadIdx.x] += ra[threadIdx.x + h];
+            rb[threadIdx.x] += rb[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * e] = ra[0];
+        out[2 * e + 1] = rb[0];
     }
 }
 
@@ -1149,8 +1265,14 @@ template <typename Real>
 void launch_inject(const DevParams& P, cudaStream_t st)
 {
     const int block = 256;
-    const size_t smem = sizeof(int) * (2 * P.ny * P.nz + 1 + block + INJ);
+    const size_t smem = sizeof(long long) * block + sizeof(int) * (2 * P.ny * P.nz + 1 + INJ);
     k_inject<Real><<<P.n_ens, block, smem, st>>>(P);
+}
+
+template <typename Real>
+void launch_free_counts(const DevParams& P, long long* out, cudaStream_t st)
+{
+    k_free_counts<Real><<<P.n_ens, 256, 0, st>>>(P, out);
 }
 
 }  // namespace emc

@@ -43,6 +43,7 @@ class EmcConfig(C.Structure):
         ("gate_x0", C.c_double), ("gate_x1", C.c_double),
         ("Vs", C.c_double), ("Vd", C.c_double), ("Vg", C.c_double), ("p_specular", C.c_double),
         ("n_particles", C.c_int64), ("capacity", C.c_int64),
+        ("shard_n_global", C.c_int64), ("shard_live_base", C.c_int64), ("shard_spare_base", C.c_int64),
         ("Z", C.c_int32 * 3), ("geometry", C.c_int32), ("n_bins", C.c_int32),
         ("steps_per_poisson", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
         ("gate_on", C.c_int32), ("seed", C.c_uint32), ("mech_mask", C.c_uint32),
@@ -85,6 +86,8 @@ def lib():
         L.emc_state_size.argtypes = [P, C.POINTER(C.c_size_t)]
         L.emc_get_state.argtypes = [P, P, C.c_size_t]
         L.emc_set_state.argtypes = [P, P, C.c_size_t]
+        L.emc_shard_counts.argtypes = [P, P, P]
+        L.emc_shard_tail.argtypes = [P, P, P, P, I32]
         L.emc_profile.argtypes = [P, I32]
         L.emc_profile_read.argtypes = [P, dp, C.POINTER(I64)]
         L.emc_debug_philox.argtypes = [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(U32), I32]
@@ -101,7 +104,7 @@ def lib():
                   "emc_poisson_solve_static", "emc_set_bias",
                   "emc_set_bias_all", "emc_set_temperature", "emc_profile", "emc_profile_read",
                   "emc_debug_philox", "emc_debug_particles", "emc_debug_tables", "emc_shape",
-                  "emc_state_size", "emc_get_state", "emc_set_state"):
+                  "emc_state_size", "emc_get_state", "emc_set_state", "emc_shard_counts", "emc_shard_tail"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -123,6 +126,9 @@ def make_config(d: dict, precision: int = FP32) -> EmcConfig:
     c.gate_x0, c.gate_x1 = d["gate_x0"], d["gate_x1"]
     c.Vs, c.Vd, c.Vg, c.p_specular = d["Vs"], d["Vd"], d["Vg"], d["p_specular"]
     c.n_particles, c.capacity = int(d["n_particles"]), int(d["capacity"])
+    c.shard_n_global = int(d.get("shard_n_global", 0))
+    c.shard_live_base = int(d.get("shard_live_base", 0))
+    c.shard_spare_base = int(d.get("shard_spare_base", 0))
     c.Z[:] = d["Z"]
     c.geometry, c.n_bins, c.steps_per_poisson = d["geometry"], d["n_bins"], d["steps_per_poisson"]
     c.nx, c.ny, c.nz, c.gate_on = d["nx"], d["ny"], d["nz"], d["gate_on"]
@@ -308,6 +314,24 @@ class Context:
         """Restore a state from emc_get_state of a context of the same ensembles."""
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         self._check(lib().emc_set_state(self.h, b.ctypes.data_as(C.c_void_p), b.nbytes))
+
+    def emc_shard_counts(self):
+        """(charge int32[E][C], free int64[E][2]) of a sharded context waiting
+        for its exchange: its own electron count per subcell and its free ids
+        among the initial-electron and the spare ids."""
+        q = np.zeros((self.n_ens, self.n_cell), dtype=np.int32)
+        f = np.zeros((self.n_ens, 2), dtype=np.int64)
+        self._check(lib().emc_shard_counts(self.h, q.ctypes.data_as(C.c_void_p), f.ctypes.data_as(C.c_void_p)))
+        return q, f
+
+    def emc_shard_tail(self, charge_global, free_prefix, free_total, lead: bool):
+        """Refill and Poisson update of a sharded context from the wire's
+        count (emc_shard_tail)."""
+        q = np.ascontiguousarray(charge_global, dtype=np.int32).reshape(self.n_ens, self.n_cell)
+        p = np.ascontiguousarray(free_prefix, dtype=np.int64).reshape(self.n_ens, 2)
+        t = np.ascontiguousarray(free_total, dtype=np.int64).reshape(self.n_ens, 2)
+        self._check(lib().emc_shard_tail(self.h, q.ctypes.data_as(C.c_void_p), p.ctypes.data_as(C.c_void_p),
+                                         t.ctypes.data_as(C.c_void_p), int(bool(lead))))
 
     def emc_surrogate_train(self, net: "EmcMlpConfig", X, Y, steps, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
                             eps=1e-8, seed=0):

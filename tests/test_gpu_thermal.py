@@ -56,8 +56,9 @@ def test_electrothermal_surrogate_gains(emc):
     Monte Carlo noise)), and the plain Monte Carlo judge finds the same peak
     rise at both results (within 3% or 3 standard errors).  What the network
     gains is accuracy per Monte Carlo run: the warm start's first iterate is
-    closer to the judged peak than the plain loop's, and it reaches 2% of it
-    in fewer Monte Carlo runs.  (Runs to the stop test are reported by the
+    closer to the judged peak than the plain loop's, and it reaches 2%, 1% and
+    0.5% of it (or the judge's noise) in no more Monte Carlo runs, and one of
+    them in fewer.  (Runs to the stop test are reported by the
     bench: near the Monte Carlo noise they are not shortened.)"""
     from paper_1707_09073_gb300 import electrothermal as ET
     from paper_1707_09073_gb300 import surrogate as S
@@ -86,10 +87,13 @@ def test_electrothermal_surrogate_gains(emc):
     assert first_s.max() < first_p.max(), (first_s, first_p)
 
     def runs_to(hist, tol):
-        return next((i + 1 for i, h in enumerate(hist) if np.all(np.abs(h - jp["peak"]) <= tol * jp["peak"])),
-                    len(hist) + 1)
+        # within tol of the judged peak, or within the judge's noise
+        lim = np.maximum(tol * jp["peak"], 3 * jp["peak_se"])
+        return next((i + 1 for i, h in enumerate(hist) if np.all(np.abs(h - jp["peak"]) <= lim)), len(hist) + 1)
 
-    assert runs_to(rs["history"], 0.02) < runs_to(rp["history"], 0.02), (rs["history"], rp["history"], jp["peak"])
+    tols = (0.02, 0.01, 0.005)
+    rs_n, rp_n = [runs_to(rs["history"], t) for t in tols], [runs_to(rp["history"], t) for t in tols]
+    assert all(a <= b for a, b in zip(rs_n, rp_n)) and rs_n != rp_n, (rs_n, rp_n, rs["history"], rp["history"])
 
 
 def test_thermal_solve_with_interface_of_eqs_2_and_3(emc):

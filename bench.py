@@ -394,6 +394,7 @@ def batched_mixed(args, stream) -> dict:
                     ctx.emc_step(STEPS_PER_POISSON)
             for ctx in ctxs:
                 ctx.emc_tally(emc.TALLY_OBS, reset=True)
+                ctx.emc_profile(True)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -404,13 +405,38 @@ def batched_mixed(args, stream) -> dict:
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
+            prof = [ctx.emc_profile_read() for ctx in ctxs]
+            for ctx in ctxs:
+                ctx.emc_profile(False)
             real = sum(int(ctx.emc_tally(emc.TALLY_EVENTS).sum()) for ctx in ctxs)
-            obs = [o for ctx in ctxs for o in ctx.emc_tally(emc.TALLY_OBS)]
+            obs = [o for ctx in ctxs for o in ctx.emc_tally(emc.TALLY_OBS, reset=True)]
+            # end to end: every step's observables of every ensemble read
+            # back into page-locked host buffers (double-buffered)
+            bufs = [[ctx.pinned_tally(emc.TALLY_OBS) for ctx in ctxs] for _ in range(2)]
+            done = [torch.cuda.Event() for _ in range(2)]
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for i in range(args.batched_steps):
+                for ctx, ob in zip(ctxs, bufs[i % 2]):
+                    ctx.emc_step(STEPS_PER_POISSON)
+                    ctx.emc_tally_async(emc.TALLY_OBS, ob)
+                done[i % 2].record(stream)
+                if i > 0:
+                    done[(i - 1) % 2].synchronize()
+            done[(args.batched_steps - 1) % 2].synchronize()
+            e2e_s = time.perf_counter() - w0
+            real2 = sum(int(ctx.emc_tally(emc.TALLY_EVENTS, reset=True).sum()) for ctx in ctxs)
+            d2h = sum(b.nbytes for b in bufs[0])
     finally:
         for ctx in ctxs:
             ctx.close()
     selfe = sum(int(o["self_events"].sum()) for o in obs)
     psteps = sum(int(o["n_samples"]) for o in obs)
+    flight_ms = sum(p[0] for p in prof)
+    ops = OPS_REAL * real + OPS_SELF * selfe + OPS_STEP * psteps
+    peaks = load_peaks()
+    peak = N_SM * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops / (flight_ms * 1e-3) / 1e12 if flight_ms > 0 else None
     return {
         "workload": "256 independent ensembles: N ~ 10^U(4,6) (sum %d), |E| ~ U(0,400) kV/cm, T ~ U(300,600) K, "
                     "N_d ~ 10^U(16,19) cm^-3; 192 bulk (field along c) + 64 half nanowires (V_d = |E| x 1 um, "
@@ -418,7 +444,46 @@ def batched_mixed(args, stream) -> dict:
         "steps": args.batched_steps, "ms_per_step": ms / args.batched_steps,
         "events_per_s": real / (ms * 1e-3), "events_incl_self_per_s": (real + selfe) / (ms * 1e-3),
         "particle_steps_per_s": psteps / (ms * 1e-3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "k_flight<float, bulk> and k_flight<float, nanowire> (one launch per context and step)",
+                     "flight_share_of_step": flight_ms / ms if ms > 0 else None,
+                     "basis": "the op model of the headline roofline over the CUDA-event time of the flight launches"},
+        "e2e": {"value": real2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+                "steps": args.batched_steps,
+                "path": "emc_step + emc_tally_async OBS of every ensemble into pinned host buffers, double-buffered"},
     }
+
+
+def sharded_wire(args, cfgs, shards: int) -> dict:
+    """The bias sweep's wires, each wire's particles sharded over `shards`
+    contexts on this GPU with the integer charge exchange on the host at the
+    end of every Poisson period (the multi-GPU protocol run on one GPU), and
+    the same wires unsharded, both timed by the wall clock around the same
+    number of steps (the sharded path synchronises at every exchange)."""
+    import numpy as np
+    import torch
+    import paper_1707_09073_gb300 as emc
+    from paper_1707_09073_gb300 import shard as SH
+    steps = STEPS_PER_POISSON * args.shard_periods
+    out = {"shards": shards, "steps": steps, "workload": "the bias sweep (21 wires), particles split over shards"}
+    for name, make in (("unsharded", lambda: emc.Context(cfgs)),
+                       ("sharded", lambda: SH.LocalWire(cfgs, shards))):
+        w = make()
+        try:
+            w.emc_step(3 * STEPS_PER_POISSON)
+            w.emc_tally(emc.TALLY_EVENTS, reset=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            w.emc_step(steps)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            ev = int(np.asarray(w.emc_tally(emc.TALLY_EVENTS)).sum())
+        finally:
+            w.close()
+        out[name] = {"events_per_s": ev / dt, "ms_per_step": 1e3 * dt / steps}
+    out["sharded_over_unsharded"] = out["sharded"]["events_per_s"] / out["unsharded"]["events_per_s"]
+    return out
 
 
 # --------------------------------------------------------------------- GPU
@@ -570,6 +635,11 @@ def run_emc(args, world: int, rank: int, local: int):
                "single_thread": {"value": s1["events"] / s1["seconds"], "unit": UNIT, "cores": 1,
                                  "sample": "%d Poisson periods (%.1f s)" % (s1["periods"], s1["seconds"])}}
 
+    shw = None
+    if world == 1 and args.shards > 1:
+        torch.cuda.synchronize(dev)
+        shw = sharded_wire(args, cfgs, args.shards)
+
     mixed = None
     if world == 1 and not args.no_batched:
         torch.cuda.synchronize(dev)
@@ -599,6 +669,7 @@ def run_emc(args, world: int, rank: int, local: int):
         "iv_curve": {"unit": "[V_d (V), I_d (uA) of the half wire]", "window_fs": n_e2e * steps,
                      "points": [[v, round(i, 3)] for v, i in iv]} if world == 1 else None,
         "batched_mixed": mixed,
+        "sharded_wire": shw,
         "surrogate_vs_plain_mc": et,
     }
     print(json.dumps(line), flush=True)
@@ -624,6 +695,9 @@ def main():
     ap.add_argument("--no-electrothermal", action="store_true", help="skip the surrogate vs plain-MC comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-ensemble mixed batch")
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--shards", type=int, default=2,
+                    help="also run the sweep with each wire's particles split over this many contexts (0/1: skip)")
+    ap.add_argument("--shard-periods", type=int, default=30)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
     ap.add_argument("--et-judge-steps", type=int, default=5000)

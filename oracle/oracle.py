@@ -16,7 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
-SRC = [os.path.join(HERE, "emc_oracle.c")]
+SRC = [os.path.join(HERE, "emc_oracle.c"), os.path.join(HERE, "phonon_oracle.c")]
+HDR = [os.path.join(HERE, "emc_oracle.h"), os.path.join(HERE, "phonon_oracle.h")]
 NV, NM = 3, 10
 
 Q_E = 1.602176634e-19
@@ -26,7 +27,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree;
     OpenMP for the optional particle-parallel loop, one thread by default)."""
     os.makedirs(BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(p) for p in SRC + [os.path.join(HERE, "emc_oracle.h")])
+    newest = max(os.path.getmtime(p) for p in SRC + HDR)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",

@@ -455,6 +455,79 @@ def batched_mixed(args, stream) -> dict:
     }
 
 
+def phonon_comparison(args, stream) -> dict:
+    """Phonon Monte Carlo of the transistor region for the heat the electrons
+    emit at V_d = 20 V (one wire of the sweep, 200,000 superparticles, heat
+    map over 5 ps after the 8 ps start-up): the FP32 kernel's throughput,
+    the temperature after three passes with local-temperature rates, the
+    Fourier solve of the same heat with the same boundaries (contacts at
+    300 K, the GaN/SiC interface of Eqs. (2)-(3) under the bottom face; its
+    kappa(T) with the mean free paths capped at the 120 nm cross-section,
+    where the Monte Carlo scatters at the faces), and the oracle's rate on the host
+    cores for a bounded sample of the same problem."""
+    import numpy as np
+    import paper_1707_09073_gb300 as emc
+    from paper_1707_09073_gb300 import electrothermal as ET
+    cfg = W.nanowire(n_particles=args.particles, Vd=20.0, seed=20)
+    ctx = emc.Context([cfg], stream=stream.cuda_stream)
+    try:
+        ctx.emc_step(8000)
+        ctx.emc_tally(emc.TALLY_HEAT_J, reset=True)
+        win = 5000
+        ctx.emc_step(win)
+        q = ET.heat_map(ctx, win * cfg["dt"])[0]
+        # the same phonon model on both sides (Table II, Eq. (1) at the wire's
+        # doping, the interface of Eqs. (2)-(3)); the Monte Carlo scatters at
+        # the faces themselves, the Fourier solve caps the mean free paths at
+        # the 120 nm cross-section
+        el = dict(n_e=cfg["Nd"], elec=W.ELECTRON_PHONON_GAN, substrate=W.TABLE_II_SIC)
+        tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=0.0, L_boundary=0.0, area_ratio=1.0, **el)
+        tc_f = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=0.0, L_boundary=120e-9, tol_K=1e-4, area_ratio=1.0, **el)
+        pc = emc.emc.phonon_config(emc.emc.WIRE_FACES, n_bins=1000, precision=emc.FP32, p_specular=0.0, seed=77)
+        N = args.phonon_bundles
+        emc.emc.phonon_solve(ctx, tc, pc, q, 100_000)  # warm-up
+        r = emc.emc.phonon_solve(ctx, tc, pc, q, N)
+        mc = ET.phonon_mc_temperature(ctx, tc, pc, q, N, passes=3, first=N)
+        T_f, _ = emc.emc.thermal_solve(ctx, tc_f, q[None, :])
+    finally:
+        ctx.close()
+    P = r["power_W"]
+    net = float(q.sum() * cfg["Lx"] * cfg["Ly"] * cfg["Lz"] / q.size)
+    peak_mc = float(mc["T"].max() - tc.T_sink)
+    peak_f = float(T_f[0].max() - tc.T_sink)
+    nyz = cfg["ny"] * cfg["nz"]
+    out = {
+        "workload": "heat of the V_d = 20 V wire (%d superparticles, 3x6x100 subcells) carried by %d phonon bundles, "
+                    "1000 wave-vector bins, FP32; faces: contacts isothermal 300 K, plane A specular, outer side and "
+                    "top diffuse, bottom GaN/SiC diffuse-mismatch interface" % (args.particles, N),
+        "bundles": N, "kernel_ms": r["kernel_ms"], "bundles_per_s": N / (r["kernel_ms"] * 1e-3),
+        "segments_per_bundle": r["segments"] / N, "segments_per_s": r["segments"] / (r["kernel_ms"] * 1e-3),
+        "scatterings_per_bundle": r["n_scatterings"] / N, "capped": r["capped"],
+        "absorbed_share": (np.asarray(r["absorbed"], float) / N).round(4).tolist(),
+        "heat_net_W": net, "heat_abs_W": P,
+        "peak_rise_K": {"phonon_mc": peak_mc, "fourier": peak_f, "mc_passes": mc["peak_history"]},
+        "R_th_K_per_W_half_wire": {"phonon_mc": peak_mc / net, "fourier": peak_f / net},
+        "rise_along_x_K": {"phonon_mc": (mc["T"].reshape(cfg["nx"], nyz).mean(axis=1) - 300.0)[::10].round(2).tolist(),
+                           "fourier": (T_f[0].reshape(cfg["nx"], nyz).mean(axis=1) - 300.0)[::10].round(2).tolist(),
+                           "x_um": [round((i + 0.5) / cfg["nx"] * cfg["Lx"] * 1e6, 3) for i in range(0, cfg["nx"], 10)]},
+    }
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        from oracle import phonon as PHO
+        O.build()
+        cores = O.host_cores()
+        n_cpu = max(1000, min(N, args.phonon_cpu_bundles))
+        t0 = time.perf_counter()
+        ro = PHO.solve(cfg, q, W.TABLE_II_GAN, emc.emc.WIRE_FACES, n_cpu, seed=77, nb=1000, n_e=cfg["Nd"],
+                       elec=W.ELECTRON_PHONON_GAN, substrate=W.TABLE_II_SIC, threads=cores)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ro["segments"] / dt, "unit": "segments/s", "cores": cores, "kind": "oracle",
+                               "sample": "%d bundles of the same problem (FP64 oracle, one pass at 300 K), %.1f s"
+                                         % (n_cpu, dt),
+                               "bundles_per_s": n_cpu / dt}
+    return out
+
+
 def sharded_wire(args, cfgs, shards: int) -> dict:
     """The bias sweep's wires, each wire's particles sharded over `shards`
     contexts on this GPU with the integer charge exchange on the host at the
@@ -635,6 +708,11 @@ def run_emc(args, world: int, rank: int, local: int):
                "single_thread": {"value": s1["events"] / s1["seconds"], "unit": UNIT, "cores": 1,
                                  "sample": "%d Poisson periods (%.1f s)" % (s1["periods"], s1["seconds"])}}
 
+    phon = None
+    if world == 1 and not args.no_phonon:
+        torch.cuda.synchronize(dev)
+        phon = phonon_comparison(args, stream)
+
     shw = None
     if world == 1 and args.shards > 1:
         torch.cuda.synchronize(dev)
@@ -670,6 +748,7 @@ def run_emc(args, world: int, rank: int, local: int):
                      "points": [[v, round(i, 3)] for v, i in iv]} if world == 1 else None,
         "batched_mixed": mixed,
         "sharded_wire": shw,
+        "phonon_mc": phon,
         "surrogate_vs_plain_mc": et,
     }
     print(json.dumps(line), flush=True)
@@ -698,6 +777,9 @@ def main():
     ap.add_argument("--shards", type=int, default=2,
                     help="also run the sweep with each wire's particles split over this many contexts (0/1: skip)")
     ap.add_argument("--shard-periods", type=int, default=30)
+    ap.add_argument("--no-phonon", action="store_true", help="skip the phonon Monte Carlo of the 20 V wire")
+    ap.add_argument("--phonon-bundles", type=int, default=10_000_000)
+    ap.add_argument("--phonon-cpu-bundles", type=int, default=4_000_000)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
     ap.add_argument("--et-judge-steps", type=int, default=5000)

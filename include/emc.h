@@ -447,6 +447,67 @@ emc_status emc_kappa(const emc_thermal_config* tc, const double* T, double* kapp
 emc_status emc_dmm_transmissivity(const emc_thermal_config* tc, const double* omega, double* tau12, int32_t n);
 emc_status emc_interface_conductance(const emc_thermal_config* tc, const double* T, double* G_K, int32_t n);
 
+/* Phonon Monte Carlo of the transistor region (the hybrid-method and
+ * coupling paragraphs: the phonon side takes the electrons' per-subcell heat
+ * and returns the temperature along the wire).  Energy-based deviational
+ * phonon bundles (Peraud and Hadjiconstantinou, 2011) of the phonon model
+ * of tc: three identical sine branches of the wire's Table II column,
+ * 1/tau = A w^4 + B1 w^2 T exp(-B2/T), plus v_g / L_boundary when
+ * L_boundary > 0 and the phonon-electron rate of Eq. (1) when n_e_m3 > 0.
+ * The spectrum is split into n_bins equal wave-vector bins of (0, q0); a
+ * bundle has one bin, flies at its group velocity and scatters at its rate at
+ * the temperature of the subcell it is in (T_cells rounded to whole kelvin);
+ * after a scattering it takes a new bin from C(w)/tau(w) and an isotropic
+ * direction.  A bundle starts in a subcell with probability proportional
+ * to the magnitude of that subcell's heat and carries its sign (negative
+ * heat, where the electrons absorb more phonon energy than they emit, is a
+ * phonon deficit), with a bin from the same distribution, and ends
+ * at an isothermal face or when it crosses an interface face (transmitted
+ * with the probability tau_12 of Eq. (2) into the substrate of
+ * tc->sub_k0_per_m / sub_omega_max_rad_s, else re-emitted diffusely).  Rough
+ * faces reflect specularly with probability p_specular, else diffusely
+ * (cosine law); specular faces are the symmetry planes. */
+enum { EMC_PH_SPECULAR = 0, EMC_PH_ROUGH = 1, EMC_PH_ISOTHERMAL = 2, EMC_PH_INTERFACE = 3 };
+
+typedef struct emc_phonon_config {
+    int32_t n_bins;           /* wave-vector bins (1 .. 65536) */
+    int32_t face[6];          /* EMC_PH_* of the faces x = 0, x = Lx, y = 0, y = Ly, z = 0, z = Lz;
+                                 at least one isothermal or interface face */
+    int32_t precision;        /* EMC_FP32 (production) or EMC_FP64 (parity build) */
+    double p_specular[6];     /* EMC_PH_ROUGH faces, in [0, 1] */
+    int64_t max_segments;     /* flight segments per bundle (1 .. 1e9); a bundle that
+                                 reaches it stops where it is and is counted as capped */
+    uint32_t seed;            /* Philox key word 0; word 1 is the bundle id */
+    int32_t block_size;       /* threads per block (0 = 256; multiple of 32 up to 256) */
+} emc_phonon_config;
+
+typedef struct emc_phonon_tally {
+    uint64_t absorbed[6];     /* bundles ended at each face */
+    uint64_t segments;        /* flight segments (to a scattering or a subcell face) */
+    uint64_t scatterings;
+    uint64_t capped;          /* bundles stopped by max_segments */
+    double power_W;           /* sum of |q| times the subcell volume (each bundle's
+                                 share of it is power_W / n_bundles) */
+    double kernel_ms;         /* device time of the Monte Carlo kernel */
+} emc_phonon_tally;
+
+/* Steady temperature rise of one wire of a nanowire context (its subcell
+ * grid, at most 4096 subcells; the context's stream) for the heat
+ * generation q (host double[C], W/m^3, finite, not all zero) carried by
+ * n_bundles bundles with ids first .. first + n_bundles - 1 (ids < 2^32).
+ * T_cells (host double[C], K, or NULL for tc->T_sink everywhere) sets the
+ * temperature of the scattering rates and of the heat capacity.  Outputs
+ * (host, NULL to skip): dT[C] = P t_c / (N C_tot(T_c) V_c) in K (P =
+ * power_W, t_c the signed residence time of all bundles in subcell c,
+ * accumulated in fixed point of 2^-24 ps), t_res_ps[C], scatterings[C],
+ * emitted[C] (bundles started per subcell), tally.  Runs of disjoint id
+ * ranges add up to the run of their union.  Errors: EMC_EINVAL for a bad
+ * configuration or input, EMC_ESTATE for a bulk context. */
+emc_status emc_phonon_solve(emc_ctx* ctx, const emc_thermal_config* tc, const emc_phonon_config* pc,
+                            const double* q, const double* T_cells, int64_t n_bundles, int64_t first,
+                            double* dT, double* t_res_ps, uint64_t* scatterings, uint64_t* emitted,
+                            emc_phonon_tally* tally);
+
 /* Diagnostics used by the test-suite. */
 /* Philox4x32-10 evaluated on the device for n (counter, key) pairs:
  * ctr[n][4], key[n][2] in, out[n][4] out (host arrays). */

@@ -23,8 +23,10 @@ q_b and frequency omega_b = omega_max sin(pi q_b / 2 q0):
 
 Rates are tabulated at each subcell's temperature rounded to whole kelvin.
 The steady temperature rise of subcell c is P t_c / (N C_tot V_c): P the
-emitted power, t_c the time all N bundles spent in it, C_tot = sum C_b at
-its temperature.
+sum of |q| V over the subcells, t_c the signed time all N bundles spent in
+it (a bundle carries the sign of the heat of the subcell it started in:
+negative heat, where the electrons absorb more than they emit, is a phonon
+deficit), C_tot = sum C_b at its temperature.
 """
 from __future__ import annotations
 
@@ -86,6 +88,7 @@ class Problem(C.Structure):
                 ("pad_", C.c_int32), ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
                 ("vg", C.POINTER(C.c_double)), ("rate", C.POINTER(C.c_double)), ("cdf", C.POINTER(C.c_double)),
                 ("tix", C.POINTER(C.c_int32)), ("cell_cdf", C.POINTER(C.c_double)),
+                ("cell_sign", C.POINTER(C.c_double)),
                 ("tau12", C.POINTER(C.c_double)), ("face", C.c_int32 * 6), ("p_specular", C.c_double * 6),
                 ("seed", C.c_uint32), ("pad2_", C.c_uint32), ("max_segments", C.c_int64)]
 
@@ -155,7 +158,8 @@ def tables(mat, nb, T_cells, L_b=0.0, n_e=0.0, elec=None):
 def solve(grid: dict, q, mat, faces, n_bundles: int, seed: int = 1, nb: int = 1000, T_cells=None, T_ref=300.0,
           p_specular=None, L_b=0.0, n_e=0.0, elec=None, substrate=None, max_segments=10_000_000, first=0,
           threads: int = 1) -> dict:
-    """Steady temperature rise (K) per subcell for heat q (W/m^3 per subcell)
+    """Steady temperature rise (K) per subcell for heat q (W/m^3 per subcell,
+    either sign)
     on the grid of ``grid`` (nx, ny, nz, Lx, Ly, Lz in m).  faces: six face
     kinds (x=0, x=Lx, y=0, y=Ly, z=0, z=Lz).  T_cells: the temperatures of the
     scattering rates (default T_ref everywhere)."""
@@ -168,16 +172,18 @@ def solve(grid: dict, q, mat, faces, n_bundles: int, seed: int = 1, nb: int = 10
     vg = v * 1e-3
     tau12 = np.array([TH.tau12(x, mat, substrate) for x in w]) if substrate is not None else np.zeros(nb)
     Vc = grid["Lx"] * grid["Ly"] * grid["Lz"] / Cn
-    if np.any(q < 0) or not q.sum() > 0:
-        raise ValueError("need non-negative heat with a positive total")
-    ccdf = np.cumsum(q) / q.sum()
+    aq = np.abs(q)
+    if not np.all(np.isfinite(q)) or not aq.sum() > 0:
+        raise ValueError("need finite heat, not all zero")
+    ccdf = np.cumsum(aq) / aq.sum()
     ccdf[-1] = 1.0
+    sign = np.where(q < 0, -1.0, 1.0)
     P = Problem()
     P.nx, P.ny, P.nz, P.nb, P.nt = nx, ny, nz, nb, rate.shape[0]
     P.Lx, P.Ly, P.Lz = grid["Lx"] * 1e9, grid["Ly"] * 1e9, grid["Lz"] * 1e9
-    keep = [np.ascontiguousarray(a) for a in (vg, rate, cdf, ccdf, tau12)]
+    keep = [np.ascontiguousarray(a) for a in (vg, rate, cdf, ccdf, tau12, sign)]
     dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
-    P.vg, P.rate, P.cdf, P.cell_cdf, P.tau12 = [dp(a) for a in keep]
+    P.vg, P.rate, P.cdf, P.cell_cdf, P.tau12, P.cell_sign = [dp(a) for a in keep]
     P.tix = tix.ctypes.data_as(C.POINTER(C.c_int32))
     P.face[:] = list(faces)
     P.p_specular[:] = list(p_specular) if p_specular is not None else [0.0] * 6
@@ -209,7 +215,7 @@ def solve(grid: dict, q, mat, faces, n_bundles: int, seed: int = 1, nb: int = 10
     scat = sum(t["scat"] for t in outs)
     emit = sum(t["emit"] for t in outs)
     absorbed = np.sum([np.array(t["T"].absorbed[:], dtype=np.uint64) for t in outs], axis=0)
-    power = float(q.sum() * Vc)
+    power = float(aq.sum() * Vc)
     dT = power * (t_res * 1e-12) / n_bundles / (ctot[tix] * Vc)
     return {"dT": dT, "t_res_ps": t_res, "scatterings": scat, "emitted": emit, "absorbed": absorbed,
             "segments": int(sum(t["T"].segments for t in outs)), "capped": int(sum(t["T"].capped for t in outs)),

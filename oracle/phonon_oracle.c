@@ -7,8 +7,10 @@
  * electrons emit in each subcell through the wire.  The steady temperature
  * rise follows from the energy-based deviational Monte Carlo of Peraud and
  * Hadjiconstantinou (2011): every simulated phonon bundle carries the same
- * share P / N of the emitted power P; a bundle is emitted in a subcell with
- * probability proportional to that subcell's heat, flies at the group
+ * share P / N of the power P = sum |q| V; a bundle is emitted in a subcell
+ * with probability proportional to the magnitude of that subcell's heat,
+ * and carries the heat's sign (negative where the electrons absorb more
+ * phonon energy than they emit: a deficit of phonons); it flies at the group
  * velocity of its frequency, scatters at the rate 1/tau(omega, T) of the
  * paragraph's relaxation-time model (plus, optionally, the boundary term and
  * Eq. (1), folded into the rate tables the caller passes), is re-emitted
@@ -16,7 +18,8 @@
  * isotropic direction (energy conserved bundle by bundle), and ends where it
  * leaves the domain through an isothermal face or is transmitted into the
  * substrate (Eq. (2)).  The deviational energy of subcell c is P times the
- * mean time a bundle spends there; divided by C V it is the temperature rise.
+ * mean signed time a bundle spends there; divided by C V it is the
+ * temperature rise.
  *
  * Frequencies are binned (the caller's bins; a bundle uses its bin's group
  * velocity and rates).  Lengths in nm, times in ps.
@@ -140,6 +143,7 @@ void ph_run(const ph_problem* P, int64_t first, int64_t n, ph_tally* T)
         double p[3];
         for (int a = 0; a < 3; ++a) p[a] = (ix[a] + u[1 + a]) * h[a];
         T->emitted[c] += 1;
+        const double sg = P->cell_sign[c];
         draw4(&s, u);
         int b = inverse_cdf(P->cdf + (size_t)P->tix[c] * nb, nb, u[0]);
         double d[3];
@@ -171,7 +175,7 @@ void ph_run(const ph_problem* P, int64_t first, int64_t n, ph_tally* T)
             const double t_scat = r > 0.0 ? depth / r : INFINITY;
             if (t_scat < t_exit) {
                 for (int a = 0; a < 3; ++a) p[a] += v * d[a] * t_scat;
-                T->t_res[c] += t_scat;
+                T->t_res[c] += sg * t_scat;
                 T->scatterings[c] += 1;
                 draw4(&s, u);
                 b = inverse_cdf(P->cdf + (size_t)P->tix[c] * nb, nb, u[0]);
@@ -180,7 +184,7 @@ void ph_run(const ph_problem* P, int64_t first, int64_t n, ph_tally* T)
                 continue;
             }
             for (int a = 0; a < 3; ++a) p[a] += v * d[a] * t_exit;
-            T->t_res[c] += t_exit;
+            T->t_res[c] += sg * t_exit;
             depth -= r * t_exit;
             if (depth < 0.0) depth = 0.0;
             const int up = d[ax] > 0.0;

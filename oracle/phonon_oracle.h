@@ -12,7 +12,8 @@ typedef struct {
     const double* rate;         /* [nt][nb] scattering rate 1/tau, 1/ps */
     const double* cdf;          /* [nt][nb] cumulative of C / tau (last = 1) */
     const int32_t* tix;         /* [C] rate table of each subcell */
-    const double* cell_cdf;     /* [C] cumulative of the subcells' heat (last = 1) */
+    const double* cell_cdf;     /* [C] cumulative of the subcells' |heat| (last = 1) */
+    const double* cell_sign;    /* [C] +1, or -1 where the heat is negative */
     const double* tau12;        /* [nb] interface transmissivity (PH_INTERFACE faces) */
     int32_t face[6];            /* faces x=0, x=Lx, y=0, y=Ly, z=0, z=Lz */
     double p_specular[6];       /* PH_ROUGH faces */

@@ -21,6 +21,7 @@
 
 #include "../../include/emc.h"
 #include "common.cuh"
+#include "phonon.cuh"
 
 namespace emc {
 // accessors of the context (defined in emc.cu)
@@ -368,6 +369,166 @@ __global__ void __launch_bounds__(512) k_thermal(TGeo G, const double* __restric
     }
 }
 
+
+// ------------------------------------------------------------ phonon MC
+// Spectral tables of the phonon Monte Carlo: nb equal wave-vector bins of
+// (0, q0), each standing for its centre q_b, w_b = w_max sin(pi q_b / 2 q0),
+// v_b = (pi w_max / 2 q0) cos(pi q_b / 2 q0), heat capacity per unit volume
+// of three branches C_b = 3 hbar w_b dn/dT q_b^2 dq / (2 pi^2); per distinct
+// whole-kelvin temperature the rates 1/tau_b and the cumulative of
+// C_b / tau_b (the re-emission distribution).
+struct PhTables {
+    std::vector<double> vg;       // [nb] nm/ps
+    std::vector<double> rate;     // [nt][nb] 1/ps
+    std::vector<double> cdf;      // [nt][nb]
+    std::vector<double> ctot;     // [nt] J/(m^3 K)
+    std::vector<int> tix;         // [C]
+    std::vector<double> tau12;    // [nb]
+};
+
+const char* ph_tables(const emc_thermal_config& tc, int nb, const std::vector<double>& T_cells, bool interface,
+                      PhTables* out)
+{
+    const double q0 = tc.k0_per_m, wm = tc.omega_max_rad_s, dq = q0 / nb;
+    std::vector<double> w(nb), v(nb), modes(nb);
+    out->vg.resize(nb);
+    out->tau12.assign(nb, 0.0);
+    for (int i = 0; i < nb; ++i) {
+        const double q = (i + 0.5) * dq;
+        w[i] = wm * std::sin(kPi * q / (2.0 * q0));
+        v[i] = wm * kPi / (2.0 * q0) * std::cos(kPi * q / (2.0 * q0));
+        modes[i] = q * q * dq / (2.0 * kPi * kPi);
+        out->vg[i] = v[i] * 1e-3;
+        if (interface) out->tau12[i] = dmm_tau12(w[i], tc);
+    }
+    std::map<long long, int> key_of;
+    out->tix.resize(T_cells.size());
+    for (double T : T_cells) key_of.emplace((long long)std::floor(T + 0.5), 0);
+    int nt = 0;
+    for (auto& kv : key_of) kv.second = nt++;
+    for (size_t c = 0; c < T_cells.size(); ++c) out->tix[c] = key_of[(long long)std::floor(T_cells[c] + 0.5)];
+    out->rate.assign((size_t)nt * nb, 0.0);
+    out->cdf.assign((size_t)nt * nb, 0.0);
+    out->ctot.assign(nt, 0.0);
+    for (const auto& kv : key_of) {
+        const double T = double(kv.first);
+        const int t = kv.second;
+        const double EF = tc.n_e_m3 > 0.0 ? fermi_level(tc.n_e_m3, T, tc.m_e_rel) : 0.0;
+        double acc = 0.0, ct = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            double r = tc.A_s3 * std::pow(w[i], 4) + tc.B1_s_per_K * w[i] * w[i] * T * std::exp(-tc.B2_K / T);
+            if (tc.L_boundary > 0.0) r += v[i] / tc.L_boundary;
+            if (tc.n_e_m3 > 0.0) r += tau_e_inv(w[i], T, EF, tc);
+            const double x = kHbar * w[i] / (kKB * T);
+            double dndT = 0.0;
+            if (x < 700.0) {
+                const double em1 = std::expm1(x);
+                dndT = x * std::exp(x) / (em1 * em1) / T;
+            }
+            const double cb = 3.0 * kHbar * w[i] * dndT * modes[i];
+            out->rate[(size_t)t * nb + i] = r * 1e-12;
+            acc += cb * r;
+            out->cdf[(size_t)t * nb + i] = acc;
+            ct += cb;
+        }
+        if (!(acc > 0.0) || !std::isfinite(acc)) return "phonon MC: no scattering weight at some temperature";
+        for (int i = 0; i < nb; ++i) out->cdf[(size_t)t * nb + i] /= acc;
+        out->cdf[(size_t)t * nb + nb - 1] = 1.0;
+        out->ctot[t] = ct;
+    }
+    return nullptr;
+}
+
+template <typename Real>
+std::vector<Real> as_real(const std::vector<double>& a)
+{
+    return std::vector<Real>(a.begin(), a.end());
+}
+
+template <typename Real>
+emc_status phonon_run(emc_ctx* ctx, const emc_phonon_config& pc, const PhTables& tb, const std::vector<double>& ccdf,
+                      const std::vector<int>& neg,
+                      int nx, int ny, int nz, double Lx, double Ly, double Lz, int64_t n, int64_t first,
+                      std::vector<unsigned long long>* t_res, std::vector<unsigned long long>* scat,
+                      std::vector<unsigned long long>* emit, unsigned long long out8[8], float* ms)
+{
+    cudaStream_t st = ctx_stream(ctx);
+    const int C = nx * ny * nz, nb = pc.n_bins, nt = (int)tb.ctot.size();
+#define PCK(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) return ctx_fail(ctx, EMC_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+    const std::vector<Real> vg = as_real<Real>(tb.vg), rate = as_real<Real>(tb.rate), cdf = as_real<Real>(tb.cdf),
+                            cc = as_real<Real>(ccdf), t12 = as_real<Real>(tb.tau12);
+    Real *d_vg, *d_rate, *d_cdf, *d_cc, *d_t12;
+    int *d_tix, *d_neg;
+    unsigned long long* d_u;  // next, out[8], t_res[C], scat[C], emit[C]
+    PCK(cudaMallocAsync(&d_vg, sizeof(Real) * nb, st));
+    PCK(cudaMallocAsync(&d_rate, sizeof(Real) * nt * nb, st));
+    PCK(cudaMallocAsync(&d_cdf, sizeof(Real) * nt * nb, st));
+    PCK(cudaMallocAsync(&d_cc, sizeof(Real) * C, st));
+    PCK(cudaMallocAsync(&d_t12, sizeof(Real) * nb, st));
+    PCK(cudaMallocAsync(&d_tix, sizeof(int) * C, st));
+    PCK(cudaMallocAsync(&d_neg, sizeof(int) * C, st));
+    const size_t nu = 9 + 3 * (size_t)C;
+    PCK(cudaMallocAsync(&d_u, sizeof(unsigned long long) * nu, st));
+    PCK(cudaMemcpyAsync(d_vg, vg.data(), sizeof(Real) * nb, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_rate, rate.data(), sizeof(Real) * nt * nb, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_cdf, cdf.data(), sizeof(Real) * nt * nb, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_cc, cc.data(), sizeof(Real) * C, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_t12, t12.data(), sizeof(Real) * nb, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_tix, tb.tix.data(), sizeof(int) * C, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_neg, neg.data(), sizeof(int) * C, cudaMemcpyHostToDevice, st));
+    PCK(cudaMemsetAsync(d_u, 0, sizeof(unsigned long long) * nu, st));
+    PhParams P{};
+    P.nx = nx; P.ny = ny; P.nz = nz; P.ncell = C; P.nb = nb;
+    P.hx = Lx * 1e9 / nx; P.hy = Ly * 1e9 / ny; P.hz = Lz * 1e9 / nz;
+    P.vg = d_vg; P.rate = d_rate; P.cdf = d_cdf; P.tix = d_tix; P.cell_cdf = d_cc; P.tau12 = d_t12;
+    P.cell_neg = d_neg;
+    for (int f = 0; f < 6; ++f) {
+        P.face[f] = pc.face[f];
+        P.p_spec[f] = pc.p_specular[f];
+    }
+    P.seed = pc.seed;
+    P.n_bundles = n; P.first = first; P.max_segments = pc.max_segments;
+    P.next = d_u; P.out = d_u + 1; P.t_res = d_u + 9; P.scat = d_u + 9 + C; P.emit = d_u + 9 + 2 * (size_t)C;
+    const int block = pc.block_size ? pc.block_size : 256;
+    const size_t smem = ph_smem_bytes<Real>(C);
+    PCK(cudaFuncSetAttribute(k_phonon<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, nsm = 0, occ = 0;
+    PCK(cudaGetDevice(&dev));
+    PCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phonon<Real>, block, smem));
+    long long grid = (long long)nsm * (occ > 0 ? occ : 1);
+    const long long need = (n + block - 1) / block;
+    if (grid > need) grid = need;
+    cudaEvent_t e0, e1;
+    PCK(cudaEventCreate(&e0));
+    PCK(cudaEventCreate(&e1));
+    PCK(cudaEventRecord(e0, st));
+    k_phonon<Real><<<(unsigned)grid, block, smem, st>>>(P);
+    ctx_count_launches(ctx, 1);
+    PCK(cudaGetLastError());
+    PCK(cudaEventRecord(e1, st));
+    std::vector<unsigned long long> u(nu);
+    PCK(cudaMemcpyAsync(u.data(), d_u, sizeof(unsigned long long) * nu, cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+    PCK(cudaEventElapsedTime(ms, e0, e1));
+    PCK(cudaEventDestroy(e0));
+    PCK(cudaEventDestroy(e1));
+    for (void* ptr : {(void*)d_vg, (void*)d_rate, (void*)d_cdf, (void*)d_cc, (void*)d_t12, (void*)d_tix, (void*)d_neg,
+                      (void*)d_u})
+        PCK(cudaFreeAsync(ptr, st));
+    PCK(cudaStreamSynchronize(st));
+#undef PCK
+    for (int k = 0; k < 8; ++k) out8[k] = u[1 + k];
+    t_res->assign(u.begin() + 9, u.begin() + 9 + C);
+    scat->assign(u.begin() + 9 + C, u.begin() + 9 + 2 * C);
+    emit->assign(u.begin() + 9 + 2 * C, u.begin() + 9 + 3 * C);
+    return EMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -454,6 +615,87 @@ emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const d
     if (d_gif) TCK(cudaFreeAsync(d_gif, st));
     TCK(cudaStreamSynchronize(st));
 #undef TCK
+    return EMC_OK;
+}
+
+emc_status emc_phonon_solve(emc_ctx* ctx, const emc_thermal_config* tc, const emc_phonon_config* pc,
+                            const double* q, const double* T_cells, int64_t n_bundles, int64_t first,
+                            double* dT, double* t_res_ps, uint64_t* scatterings, uint64_t* emitted,
+                            emc_phonon_tally* tally)
+{
+    if (!ctx || !tc || !pc || !q) return EMC_EINVAL;
+    int nx, ny, nz, ne;
+    double Lx, Ly, Lz;
+    if (!ctx_grid(ctx, &nx, &ny, &nz, &Lx, &Ly, &Lz, &ne))
+        return ctx_fail(ctx, EMC_ESTATE, "emc_phonon_solve needs the nanowire geometry");
+    const int C = nx * ny * nz;
+    if (C > 4096) return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: at most 4096 subcells");
+    bool absorbing = false, interface = false;
+    for (int f = 0; f < 6; ++f) {
+        if (pc->face[f] < EMC_PH_SPECULAR || pc->face[f] > EMC_PH_INTERFACE || !(pc->p_specular[f] >= 0.0) ||
+            !(pc->p_specular[f] <= 1.0))
+            return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: face kinds and p_specular in [0, 1]");
+        absorbing |= pc->face[f] == EMC_PH_ISOTHERMAL || pc->face[f] == EMC_PH_INTERFACE;
+        interface |= pc->face[f] == EMC_PH_INTERFACE;
+    }
+    if (!absorbing) return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: no isothermal or interface face");
+    if (pc->n_bins < 1 || pc->n_bins > 65536 || pc->max_segments < 1 || pc->max_segments > 1000000000 ||
+        (pc->precision != EMC_FP32 && pc->precision != EMC_FP64) ||
+        (pc->block_size != 0 && (pc->block_size < 32 || pc->block_size > 256 || pc->block_size % 32)))
+        return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: n_bins, max_segments, precision or block_size");
+    if (n_bundles < 1 || first < 0 || first + n_bundles > (int64_t(1) << 32))
+        return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: bundle ids first .. first + n - 1 must lie in [0, 2^32)");
+    if (!(tc->k0_per_m > 0) || !(tc->omega_max_rad_s > 0) || tc->A_s3 < 0 || tc->B1_s_per_K < 0 || tc->B2_K < 0 ||
+        tc->L_boundary < 0 || !electrons_ok(*tc) || (interface && !dmm_ok(*tc)))
+        return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: invalid phonon model");
+    double qsum = 0.0;  // sum |q|
+    std::vector<int> neg(C);
+    for (int c = 0; c < C; ++c) {
+        if (!std::isfinite(q[c])) return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: q must be finite");
+        qsum += std::fabs(q[c]);
+        neg[c] = q[c] < 0.0 ? 1 : 0;
+    }
+    if (!(qsum > 0.0)) return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: no heat");
+    std::vector<double> Tc(C, tc->T_sink);
+    if (T_cells)
+        for (int c = 0; c < C; ++c) Tc[c] = T_cells[c];
+    for (int c = 0; c < C; ++c)
+        if (!(Tc[c] >= 1.0 && Tc[c] <= 1e5)) return ctx_fail(ctx, EMC_EINVAL, "emc_phonon_solve: temperatures in [1, 1e5] K");
+    PhTables tb;
+    if (const char* e = ph_tables(*tc, pc->n_bins, Tc, interface, &tb)) return ctx_fail(ctx, EMC_EINVAL, e);
+    std::vector<double> ccdf(C);
+    double acc = 0.0;
+    for (int c = 0; c < C; ++c) {
+        acc += std::fabs(q[c]);
+        ccdf[c] = acc / qsum;
+    }
+    ccdf[C - 1] = 1.0;
+    std::vector<unsigned long long> tr, sc, em;
+    unsigned long long out8[8];
+    float ms = 0.f;
+    const emc_status s =
+        pc->precision == EMC_FP64
+            ? phonon_run<double>(ctx, *pc, tb, ccdf, neg, nx, ny, nz, Lx, Ly, Lz, n_bundles, first, &tr, &sc, &em, out8, &ms)
+            : phonon_run<float>(ctx, *pc, tb, ccdf, neg, nx, ny, nz, Lx, Ly, Lz, n_bundles, first, &tr, &sc, &em, out8, &ms);
+    if (s != EMC_OK) return s;
+    const double Vc = Lx * Ly * Lz / C, power = qsum * Vc;
+    uint64_t nscat = 0;
+    for (int c = 0; c < C; ++c) {
+        const double t_ps = double((long long)tr[c]) / kPhTimeScale;  // two's complement: signed
+        if (t_res_ps) t_res_ps[c] = t_ps;
+        if (dT) dT[c] = power * (t_ps * 1e-12) / double(n_bundles) / (tb.ctot[tb.tix[c]] * Vc);
+        if (scatterings) scatterings[c] = sc[c];
+        if (emitted) emitted[c] = em[c];
+        nscat += sc[c];
+    }
+    if (tally) {
+        for (int f = 0; f < 6; ++f) tally->absorbed[f] = out8[f];
+        tally->segments = out8[6];
+        tally->capped = out8[7];
+        tally->scatterings = nscat;
+        tally->power_W = power;
+        tally->kernel_ms = ms;
+    }
     return EMC_OK;
 }
 

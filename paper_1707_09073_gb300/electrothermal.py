@@ -53,6 +53,22 @@ def thermal_resistance(T: np.ndarray, power: np.ndarray, T_sink: float) -> np.nd
         return np.where(power > 0, rise / power, np.nan)
 
 
+def phonon_mc_temperature(ctx, tc, pc, q: np.ndarray, n_bundles: int, passes: int = 3, first: int = 0) -> dict:
+    """Temperature (K) per subcell of the first wire of a nanowire context
+    from the phonon Monte Carlo (emc_phonon_solve) for the heat q [C]
+    (W/m^3): each pass takes the scattering rates and heat capacity at the
+    temperatures of the previous pass (the first at T_sink; the coupling
+    paragraph's local temperature) and fresh bundle ids.  Returns the
+    temperatures, the peak rise after each pass and the last pass."""
+    T = np.full(ctx.n_cell, tc.T_sink)
+    peaks, r = [], None
+    for k in range(passes):
+        r = _emc.phonon_solve(ctx, tc, pc, q, n_bundles, T_cells=T, first=first + k * n_bundles)
+        T = tc.T_sink + r["dT"]
+        peaks.append(float(r["dT"].max()))
+    return {"T": T, "peak_history": peaks, "last": r}
+
+
 def mc_heat_halves(ctx, T: np.ndarray, warm_steps: int, avg_steps: int):
     """Heat maps of the two halves of the averaging window after warm_steps
     at the subcell temperatures T, and their mean (W/m^3): the halves are

@@ -499,6 +499,61 @@ def thermal_solve(ctx: "Context", tc: EmcThermalConfig, q, T0=None):
     return T, it
 
 
+# ------------------------------------------------------------ phonon MC
+PH_SPECULAR, PH_ROUGH, PH_ISOTHERMAL, PH_INTERFACE = 0, 1, 2, 3
+# the half wire: contacts isothermal, symmetry plane A specular, the outer
+# side and the top rough, the bottom on the substrate's interface
+WIRE_FACES = (PH_ISOTHERMAL, PH_ISOTHERMAL, PH_SPECULAR, PH_ROUGH, PH_INTERFACE, PH_ROUGH)
+
+
+class EmcPhononConfig(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("face", C.c_int32 * 6), ("precision", C.c_int32),
+                ("p_specular", C.c_double * 6), ("max_segments", C.c_int64), ("seed", C.c_uint32),
+                ("block_size", C.c_int32)]
+
+
+class EmcPhononTally(C.Structure):
+    _fields_ = [("absorbed", C.c_uint64 * 6), ("segments", C.c_uint64), ("scatterings", C.c_uint64),
+                ("capped", C.c_uint64), ("power_W", C.c_double), ("kernel_ms", C.c_double)]
+
+
+def phonon_config(faces=WIRE_FACES, n_bins=1000, precision=FP32, p_specular=0.0, max_segments=10_000_000, seed=1,
+                  block_size=0) -> EmcPhononConfig:
+    pc = EmcPhononConfig()
+    pc.n_bins = n_bins
+    pc.face[:] = list(faces)
+    pc.precision = precision
+    pc.p_specular[:] = list(p_specular) if np.ndim(p_specular) else [float(p_specular)] * 6
+    pc.max_segments, pc.seed, pc.block_size = int(max_segments), int(seed) & 0xFFFFFFFF, block_size
+    return pc
+
+
+def phonon_solve(ctx: "Context", tc: EmcThermalConfig, pc: EmcPhononConfig, q, n_bundles: int, T_cells=None,
+                 first: int = 0) -> dict:
+    """Phonon Monte Carlo of one wire of a nanowire context
+    (emc_phonon_solve): temperature rise dT [C] (K) for heat q [C] (W/m^3),
+    residence times, scatterings and emissions per subcell, the tally."""
+    L = lib()
+    if not getattr(L, "_phonon_ready", False):
+        L.emc_phonon_solve.argtypes = [C.c_void_p, C.POINTER(EmcThermalConfig), C.POINTER(EmcPhononConfig),
+                                       C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.POINTER(EmcPhononTally)]
+        L.emc_phonon_solve.restype = C.c_int
+        L._phonon_ready = True
+    n = ctx.n_cell
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(n)
+    Tc = None if T_cells is None else np.ascontiguousarray(T_cells, dtype=np.float64).reshape(n)
+    dT, tr = np.zeros(n), np.zeros(n)
+    sc, em = np.zeros(n, np.uint64), np.zeros(n, np.uint64)
+    t = EmcPhononTally()
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    ctx._check(L.emc_phonon_solve(ctx.h, C.byref(tc), C.byref(pc), vp(q), vp(Tc) if Tc is not None else None,
+                                  int(n_bundles), int(first), vp(dT), vp(tr), vp(sc), vp(em), C.byref(t)))
+    return {"dT": dT, "t_res_ps": tr, "scatterings": sc, "emitted": em, "absorbed": np.array(t.absorbed[:], np.uint64),
+            "segments": int(t.segments), "n_scatterings": int(t.scatterings), "capped": int(t.capped),
+            "power_W": t.power_W, "kernel_ms": t.kernel_ms}
+
+
 # ------------------------------------------------------------ surrogate MLP
 class EmcMlpConfig(C.Structure):
     _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_layers", C.c_int32), ("n_out", C.c_int32),

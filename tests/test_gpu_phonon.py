@@ -1,0 +1,169 @@
+"""Phonon Monte Carlo on the GPU (emc_phonon_solve) against the FP64 oracle
+(oracle/phonon.py): the parity build follows the oracle's bundles exactly
+(the same emissions, scatterings, segments and face counts per subcell, the
+residence times to the fixed-point rounding), the production build agrees
+in distribution, and disjoint bundle ranges add up."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import phonon as PH
+
+pytestmark = pytest.mark.gpu
+
+GAN, SIC = W.TABLE_II_GAN, W.TABLE_II_SIC
+
+
+def _wire(nx=20, Lx=200e-9):
+    return W.nanowire(n_particles=10, nx=nx, Lx=Lx, Vd=1.0, seed=3)
+
+
+def _heat(cfg, seed=0):
+    """A heat map shaped like the electrons' (rising towards the drain-side
+    gate edge), positive everywhere."""
+    C = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    rng = np.random.default_rng(seed)
+    x = (np.arange(cfg["nx"]) + 0.5) / cfg["nx"]
+    prof = 1.0 + 8.0 * np.exp(-((x - 0.75) / 0.08) ** 2)
+    return (np.repeat(prof, cfg["ny"] * cfg["nz"]) * rng.uniform(0.5, 1.5, C) * 1e17)
+
+
+def _temps(cfg, seed=1):
+    C = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    return 300.0 + np.random.default_rng(seed).uniform(0.0, 40.0, C)
+
+
+def _gpu(emc, cfg, tc, pc, q, n, T=None, first=0):
+    with emc.Context(cfg) as ctx:
+        return emc.emc.phonon_solve(ctx, tc, pc, q, n, T_cells=T, first=first)
+
+
+def _assert_same_bundles(g, r):
+    assert np.array_equal(g["emitted"], r["emitted"])
+    assert np.array_equal(g["scatterings"], r["scatterings"])
+    assert np.array_equal(g["absorbed"], r["absorbed"])
+    assert g["segments"] == r["segments"] and g["capped"] == r["capped"]
+    # residence times.  Their total is the same to rounding (the GPU rounds
+    # each segment to 2^-24 ps).  Per subcell, a bundle that grazes a
+    # subcell face splits its time between the two subcells at a point that
+    # one-ulp differences of the arithmetic (a fused multiply-add, a sine)
+    # move: the oracle built with and without fused multiply-adds differs by
+    # up to 3.5e-6 of a subcell's time on the all-rough case, with the
+    # integer tallies identical, so that is the scale allowed here.
+    assert abs(g["t_res_ps"].sum() / r["t_res_ps"].sum() - 1) < 1e-9
+    np.testing.assert_allclose(g["t_res_ps"], r["t_res_ps"], rtol=2e-5, atol=1e-6)
+    np.testing.assert_allclose(g["dT"], r["dT"], rtol=2e-5, atol=1e-9 * np.abs(r["dT"]).max())
+
+
+@pytest.mark.parametrize("case", ["wire", "eq1_boundary", "all_rough_p", "mixed_sign"])
+def test_fp64_bundles_follow_the_oracle(emc, case):
+    """FP64 parity build against the oracle, bundle for bundle, on a 20 x 3 x
+    6 wire: contacts isothermal, plane A specular, rough outer side and top,
+    the GaN/SiC interface of Eq. (2) at the bottom; subcell temperatures
+    300-340 K (several rate tables); with Eq. (1) and a boundary term; with
+    every non-absorbing face rough at p = 0.4; with negative heat (phonon
+    absorption) near the source."""
+    cfg = _wire()
+    q, T = _heat(cfg), _temps(cfg)
+    if case == "mixed_sign":
+        q[: 4 * cfg["ny"] * cfg["nz"]] *= -0.5
+    faces = list(emc.emc.WIRE_FACES)
+    p = 0.3
+    L_b, n_e, el = 0.0, 0.0, None
+    if case == "eq1_boundary":
+        L_b, n_e, el = 300e-9, 1e24, W.ELECTRON_PHONON_GAN
+    if case == "all_rough_p":
+        faces = [emc.emc.PH_ISOTHERMAL, emc.emc.PH_ROUGH, emc.emc.PH_ROUGH, emc.emc.PH_ROUGH,
+                 emc.emc.PH_INTERFACE, emc.emc.PH_ROUGH]
+        p = 0.4
+    tc = emc.emc.thermal_config(GAN, L_boundary=L_b, n_e=n_e, elec=el, substrate=SIC)
+    pc = emc.emc.phonon_config(faces, n_bins=400, precision=emc.FP64, p_specular=p, seed=9)
+    N = 20_000
+    g = _gpu(emc, cfg, tc, pc, q, N, T)
+    r = PH.solve(cfg, q, GAN, faces, N, seed=9, nb=400, T_cells=T, p_specular=[p] * 6, L_b=L_b, n_e=n_e,
+                 elec=el, substrate=SIC, threads=8)
+    assert g["capped"] == 0 and int(g["absorbed"].sum()) == N
+    _assert_same_bundles(g, r)
+
+
+def test_fp64_capped_bundles_and_ragged_counts(emc):
+    """A segment cap that stops most bundles, an odd bundle count and a
+    bundle range that does not start at 0: still bundle for bundle."""
+    cfg = _wire()
+    q = _heat(cfg, 4)
+    tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC)
+    pc = emc.emc.phonon_config(emc.emc.WIRE_FACES, n_bins=300, precision=emc.FP64, p_specular=0.2, seed=4,
+                               max_segments=40)
+    g = _gpu(emc, cfg, tc, pc, q, 1237, first=100_003)
+    r = PH.solve(cfg, q, GAN, emc.emc.WIRE_FACES, 1237, seed=4, nb=300, p_specular=[0.2] * 6, substrate=SIC,
+                 max_segments=40, first=100_003)
+    assert g["capped"] > 0
+    _assert_same_bundles(g, r)
+    assert int(g["absorbed"].sum()) + g["capped"] == 1237
+
+
+def test_disjoint_bundle_ranges_add_up(emc):
+    cfg = _wire()
+    q = _heat(cfg, 5)
+    tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC)
+    pc = emc.emc.phonon_config(emc.emc.WIRE_FACES, n_bins=300, precision=emc.FP64, seed=2)
+    a = _gpu(emc, cfg, tc, pc, q, 3000, first=0)
+    b = _gpu(emc, cfg, tc, pc, q, 5000, first=3000)
+    u = _gpu(emc, cfg, tc, pc, q, 8000, first=0)
+    for k in ("emitted", "scatterings", "absorbed", "t_res_ps"):
+        assert np.array_equal(a[k] + b[k], u[k]), k
+    assert a["segments"] + b["segments"] == u["segments"]
+
+
+def test_fp32_production_agrees_in_distribution(emc):
+    """FP32 production build, 8 batches of 40,000 bundles (disjoint ids),
+    against one FP64 oracle run of 40,000: temperature rise per x-slab and
+    the share of bundles ending at each face within 3.5 sigma."""
+    cfg = _wire()
+    q, T = _heat(cfg, 6), _temps(cfg, 7)
+    tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC)
+    pc = emc.emc.phonon_config(emc.emc.WIRE_FACES, n_bins=500, precision=emc.FP32, p_specular=0.3, seed=21)
+    N, B = 40_000, 8
+    nyz = cfg["ny"] * cfg["nz"]
+    slabs, faces = [], []
+    with emc.Context(cfg) as ctx:
+        for k in range(B):
+            g = emc.emc.phonon_solve(ctx, tc, pc, q, N, T_cells=T, first=10_000_000 + k * N)
+            assert g["capped"] == 0
+            slabs.append(g["dT"].reshape(cfg["nx"], nyz).mean(axis=1))
+            faces.append(g["absorbed"] / N)
+    r = PH.solve(cfg, q, GAN, emc.emc.WIRE_FACES, N, seed=21, nb=500, T_cells=T, p_specular=[0.3] * 6,
+                 substrate=SIC, threads=8)
+    slabs, faces = np.array(slabs), np.array(faces)
+    ref = r["dT"].reshape(cfg["nx"], nyz).mean(axis=1)
+    sd = slabs.std(axis=0, ddof=1)
+    z = (slabs.mean(axis=0) - ref) / (sd * np.sqrt(1.0 / B + 1.0))
+    assert np.abs(z).max() < 3.5, z
+    fr = r["absorbed"] / N
+    sf = np.sqrt(np.maximum(fr * (1 - fr), 1e-12) / N)
+    zf = (faces.mean(axis=0) - fr) / (sf * np.sqrt(1.0 / B + 1.0))
+    assert np.abs(zf).max() < 3.5, zf
+    assert np.abs(slabs.mean(axis=0) / ref - 1).max() < 0.05
+
+
+def test_phonon_solve_rejects_bad_input(emc):
+    cfg = _wire()
+    q = _heat(cfg)
+    tc = emc.emc.thermal_config(GAN, substrate=SIC)
+    with emc.Context(cfg) as ctx:
+        bad = [
+            (emc.emc.phonon_config([emc.emc.PH_SPECULAR] * 6), q, 10),  # no absorbing face
+            (emc.emc.phonon_config(n_bins=0), q, 10),
+            (emc.emc.phonon_config(), np.zeros_like(q), 10),             # no heat
+            (emc.emc.phonon_config(), q * np.nan, 10),
+            (emc.emc.phonon_config(), q, 0),
+            (emc.emc.phonon_config(p_specular=1.5), q, 10),
+        ]
+        for pc, qq, n in bad:
+            with pytest.raises(emc.EmcError):
+                emc.emc.phonon_solve(ctx, tc, pc, qq, n)
+        with pytest.raises(emc.EmcError):  # interface face without a substrate
+            emc.emc.phonon_solve(ctx, emc.emc.thermal_config(GAN), emc.emc.phonon_config(), q, 10)
+    with emc.Context(W.bulk(n_particles=100)) as ctx:
+        with pytest.raises(emc.EmcError):
+            emc.emc.phonon_solve(ctx, tc, emc.emc.phonon_config(), np.ones(1), 10)

@@ -158,3 +158,31 @@ def test_diffusive_slab_follows_fouriers_law():
     assert abs(got[mid].mean() / want[mid].mean() - 1) < 0.01
     # the conductivity matters: a third off would show
     assert abs(got[mid].mean() / (want[mid].mean() * 1.33) - 1) > 0.2
+
+
+def test_negative_heat_is_a_phonon_deficit():
+    """Bundles carry the sign of their subcell's heat: reversing every sign
+    reverses the temperature rise exactly (the same bundles, the same
+    paths), and a mixed-sign source is the difference of its parts within
+    the Monte Carlo noise."""
+    n = 10
+    grid = dict(nx=n, ny=2, nz=2, Lx=200e-9, Ly=40e-9, Lz=40e-9)
+    faces = [PH.ISOTHERMAL, PH.ISOTHERMAL, PH.SPECULAR, PH.ROUGH, PH.SPECULAR, PH.ROUGH]
+    rng = np.random.default_rng(2)
+    q = rng.uniform(0.5, 1.5, n * 4) * 1e18
+    q[:8] *= -1.0
+    a = PH.solve(grid, q, GAN, faces, 4000, seed=5, nb=200, p_specular=[0.5] * 6)
+    b = PH.solve(grid, -q, GAN, faces, 4000, seed=5, nb=200, p_specular=[0.5] * 6)
+    assert np.array_equal(a["dT"], -b["dT"]) and np.array_equal(a["scatterings"], b["scatterings"])
+    # superposition, in the diffusive regime (mean free path 10 nm) where a
+    # bundle's time is not dominated by rare long flights; x-slab means
+    pos, neg = np.where(q > 0, q, 0.0), np.where(q < 0, -q, 0.0)
+    N = 60_000
+    kw = dict(nb=200, p_specular=[0.5] * 6, L_b=10e-9, threads=4)
+    slab = lambda r: r["dT"].reshape(n, 4).mean(axis=1)
+    m = slab(PH.solve(grid, q, GAN_FREE, faces, N, seed=6, **kw))
+    p = slab(PH.solve(grid, pos, GAN_FREE, faces, N, seed=7, **kw))
+    g = slab(PH.solve(grid, neg, GAN_FREE, faces, N, seed=8, **kw))
+    scale = np.abs(p).max()
+    assert np.abs(m - (p - g)).max() < 0.03 * scale, (m, p - g, scale)
+    assert np.all(m[:2] < p[:2] - 0.05 * scale)  # the deficit shows near the source

@@ -10,10 +10,16 @@
 //
 // One thread per bundle at a time; a thread that finishes a bundle takes the
 // next one from a global counter, so the warps stay full until the work
-// runs out.  Per step the bundle flies to the nearest of: its next
+// runs out.  Per segment the bundle flies to the nearest of: its next
 // scattering (the optical depth left over the subcell's rate), a face of its
 // subcell (then the neighbouring subcell, with its own rate table), a face of
-// the domain (specular, rough, isothermal or interface).  Residence times,
+// the domain (specular, rough, isothermal or interface).  Each lane first
+// runs the segments that need no random numbers (subcell, specular and
+// isothermal faces: a few dozen instructions each) up to its next
+// scattering or rough / interface face; the draws and new directions of
+// those events, and the emissions of new bundles, then run with most lanes
+// of the warp together instead of once per segment for the few lanes that
+// happen to scatter in it.  Residence times,
 // scatterings and emissions are tallied per subcell in shared memory (time
 // as a 64-bit two's-complement fixed-point count of 2^-24 ps, so the sums do
 // not depend on the order of the additions) and added to global memory at
@@ -75,9 +81,12 @@ struct PhM<float> {
         *c = -cc;
     }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    // a 32-bit conversion where it fits (under 256 ps): the 64-bit one runs
+    // on the double-precision pipe
     static __device__ __forceinline__ unsigned long long fixed(float t)
     {
-        return __float2ull_rn(t * float(kPhTimeScale));
+        const float x = t * float(kPhTimeScale);
+        return x < 4.0e9f ? (unsigned long long)__float2uint_rn(x) : __float2ull_rn(x);
     }
 };
 template <>
@@ -88,22 +97,25 @@ struct PhM<double> {
     static __device__ __forceinline__ unsigned long long fixed(double t) { return __double2ull_rn(t * kPhTimeScale); }
 };
 
-// Products and sums of the flight arithmetic.  In the parity build every
-// product and sum is rounded by itself (no fused multiply-add), as the
-// oracle rounds it: a bundle that grazes a subcell face splits its time
-// between the two subcells at a point that a one-ulp difference can move
-// visibly.  The production build lets the compiler fuse them.
+// Products, sums and quotients of the flight arithmetic.  In the parity
+// build every operation is rounded by itself (no fused multiply-add, IEEE
+// division), as the oracle rounds it: a bundle that grazes a subcell face
+// splits its time between the two subcells at a point that a one-ulp
+// difference can move visibly.  The production build lets the compiler fuse
+// products and sums and divides with the hardware approximation.
 template <typename Real>
 struct PhA {
     static __device__ __forceinline__ Real mul(Real a, Real b) { return a * b; }
     static __device__ __forceinline__ Real add(Real a, Real b) { return a + b; }
     static __device__ __forceinline__ Real sub(Real a, Real b) { return a - b; }
+    static __device__ __forceinline__ Real div(Real a, Real b) { return __fdividef(a, b); }
 };
 template <>
 struct PhA<double> {
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
 };
 
 // a fixed-point time, negated (two's complement) for a negative bundle
@@ -196,120 +208,141 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
     using A = PhA<Real>;
 
     unsigned long long n_seg = 0, n_cap = 0;
-    bool active = false, neg = false;
+    // Per lane: ev = 3 wants a new bundle, 1 a scattering (or, right after
+    // an emission, the first frequency and direction), 2 a rough or
+    // interface face f; 0 flies.  The whole warp runs the loop in step: each
+    // round the flying lanes run one segment, and the pending events run
+    // (one draw each) once at least half of the lanes with work wait.
+    bool neg = false, done = false, fresh = false;
+    int ev = 3, f = 0;
     PhStream st{P.seed, 0u, 0u};
     Real p[3], d[3], depth = Real(0);
     int ix[3] = {0, 0, 0}, c = 0, b = 0;
     long long seg = 0;
     for (;;) {
-        if (!active) {
+        if (!done && ev == 0) {
+            // one flight segment (needs no random numbers)
+            if (seg >= P.max_segments) {
+                ++n_cap;
+                ev = 3;
+            } else {
+                ++seg;
+                ++n_seg;
+                const Real v = __ldg(vg + b);
+                const Real rr = __ldg(rate + (size_t)__ldg(P.tix + c) * nb + b);
+                // time to the faces of the subcell, the earliest axis first
+                int ax = 0;
+                Real t_exit = INF;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Real ta = INF;
+                    if (d[a] > Real(0)) ta = A::div(A::sub(A::mul(Real(ix[a] + 1), h[a]), p[a]), A::mul(v, d[a]));
+                    else if (d[a] < Real(0)) ta = A::div(A::sub(A::mul(Real(ix[a]), h[a]), p[a]), A::mul(v, d[a]));
+                    if (ta < Real(0)) ta = Real(0);
+                    if (ta < t_exit) {
+                        t_exit = ta;
+                        ax = a;
+                    }
+                }
+                const Real t_scat = rr > Real(0) ? A::div(depth, rr) : INF;
+                const bool scat = t_scat < t_exit;
+                const Real t = scat ? t_scat : t_exit;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) p[a] = A::add(p[a], A::mul(A::mul(v, d[a]), t));
+                atomicAdd(&s_t[c], ph_signed(PhM<Real>::fixed(t), neg));
+                if (scat) {
+                    ev = 1;
+                } else {
+                    depth = A::sub(depth, A::mul(rr, t_exit));
+                    if (depth < Real(0)) depth = Real(0);
+                    // onto the face of axis ax (constant indices only: registers)
+                    bool up = false, inside = false;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == ax) {
+                            up = d[a] > Real(0);
+                            p[a] = A::mul(Real(ix[a] + (up ? 1 : 0)), h[a]);
+                            const int nxt = ix[a] + (up ? 1 : -1);
+                            inside = nxt >= 0 && nxt < nc[a];
+                            if (inside) ix[a] = nxt;
+                        }
+                    }
+                    if (inside) {
+                        c = (ix[0] * P.ny + ix[1]) * P.nz + ix[2];
+                    } else {
+                        f = 2 * ax + (up ? 1 : 0);
+                        const int kind = P.face[f];
+                        if (kind == PH_ISOTHERMAL) {
+                            atomicAdd(&s_out[f], 1ull);
+                            ev = 3;
+                        } else if (kind == PH_SPECULAR) {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a)
+                                if (a == ax) d[a] = -d[a];
+                        } else {
+                            ev = 2;
+                        }
+                    }
+                }
+            }
+        }
+        const unsigned pend = __ballot_sync(0xFFFFFFFFu, !done && ev != 0);
+        const unsigned live = __ballot_sync(0xFFFFFFFFu, !done);
+        if (live == 0u) break;
+        if (2 * __popc(pend) < __popc(live)) continue;
+        // the pending events
+        if (!done && ev == 3) {
             const unsigned long long i = atomicAdd(P.next, 1ull);
-            if (i >= (unsigned long long)P.n_bundles) break;
-            st.id = uint32_t(P.first + (long long)i);
-            st.n = 0u;
-            U4 r = st.draw();
-            c = ph_inverse_cdf<Real>(ccdf, C, u01<Real>(r.a));
-            ix[0] = c / (P.ny * P.nz);
-            ix[1] = (c / P.nz) % P.ny;
-            ix[2] = c % P.nz;
-            p[0] = A::mul(A::add(Real(ix[0]), u01<Real>(r.b)), h[0]);
-            p[1] = A::mul(A::add(Real(ix[1]), u01<Real>(r.c)), h[1]);
-            p[2] = A::mul(A::add(Real(ix[2]), u01<Real>(r.d)), h[2]);
-            atomicAdd(&s_emit[c], 1u);
-            neg = __ldg(P.cell_neg + c) != 0;
-            r = st.draw();
-            b = ph_inverse_cdf<Real>(cdf + (size_t)__ldg(P.tix + c) * nb, nb, u01<Real>(r.a));
-            ph_isotropic<Real>(u01<Real>(r.b), u01<Real>(r.c), d[0], d[1], d[2]);
-            depth = PhM<Real>::neglog(u01<Real>(r.d));
-            seg = 0;
-            active = true;
-        }
-        if (seg >= P.max_segments) {
-            ++n_cap;
-            active = false;
-            continue;
-        }
-        ++seg;
-        ++n_seg;
-        const Real v = __ldg(vg + b);
-        const Real rr = __ldg(rate + (size_t)__ldg(P.tix + c) * nb + b);
-        // time to the faces of the subcell, the earliest axis first
-        int ax = 0;
-        Real t_exit = INF;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            Real ta = INF;
-            if (d[a] > Real(0)) ta = A::sub(A::mul(Real(ix[a] + 1), h[a]), p[a]) / A::mul(v, d[a]);
-            else if (d[a] < Real(0)) ta = A::sub(A::mul(Real(ix[a]), h[a]), p[a]) / A::mul(v, d[a]);
-            if (ta < Real(0)) ta = Real(0);
-            if (ta < t_exit) {
-                t_exit = ta;
-                ax = a;
+            if (i >= (unsigned long long)P.n_bundles) {
+                done = true;
+            } else {
+                st.id = uint32_t(P.first + (long long)i);
+                st.n = 0u;
+                const U4 r = st.draw();
+                c = ph_inverse_cdf<Real>(ccdf, C, u01<Real>(r.a));
+                ix[0] = c / (P.ny * P.nz);
+                ix[1] = (c / P.nz) % P.ny;
+                ix[2] = c % P.nz;
+                p[0] = A::mul(A::add(Real(ix[0]), u01<Real>(r.b)), h[0]);
+                p[1] = A::mul(A::add(Real(ix[1]), u01<Real>(r.c)), h[1]);
+                p[2] = A::mul(A::add(Real(ix[2]), u01<Real>(r.d)), h[2]);
+                atomicAdd(&s_emit[c], 1u);
+                neg = __ldg(P.cell_neg + c) != 0;
+                seg = 0;
+                fresh = true;
+                ev = 1;
             }
         }
-        const Real t_scat = rr > Real(0) ? depth / rr : INF;
-        if (t_scat < t_exit) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) p[a] = A::add(p[a], A::mul(A::mul(v, d[a]), t_scat));
-            atomicAdd(&s_t[c], ph_signed(PhM<Real>::fixed(t_scat), neg));
-            atomicAdd(&s_scat[c], 1u);
+        if (!done && (ev == 1 || ev == 2)) {
             const U4 r = st.draw();
-            b = ph_inverse_cdf<Real>(cdf + (size_t)__ldg(P.tix + c) * nb, nb, u01<Real>(r.a));
-            ph_isotropic<Real>(u01<Real>(r.b), u01<Real>(r.c), d[0], d[1], d[2]);
-            depth = PhM<Real>::neglog(u01<Real>(r.d));
-            continue;
-        }
+            const Real u0 = u01<Real>(r.a);
+            if (ev == 1) {
+                // a scattering, or the first flight of a new bundle
+                if (!fresh) atomicAdd(&s_scat[c], 1u);
+                fresh = false;
+                b = ph_inverse_cdf<Real>(cdf + (size_t)__ldg(P.tix + c) * nb, nb, u0);
+                ph_isotropic<Real>(u01<Real>(r.b), u01<Real>(r.c), d[0], d[1], d[2]);
+                depth = PhM<Real>::neglog(u01<Real>(r.d));
+                ev = 0;
+            } else {
+                const int ax = f >> 1;
+                bool diffuse = true;
+                ev = 0;
+                if (P.face[f] == PH_INTERFACE) {
+                    if (u0 < __ldg(tau12 + b)) {
+                        atomicAdd(&s_out[f], 1ull);
+                        diffuse = false;
+                        ev = 3;
+                    }
+                } else if (u0 < Real(P.p_spec[f])) {  // rough: specular part
+                    diffuse = false;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) p[a] = A::add(p[a], A::mul(A::mul(v, d[a]), t_exit));
-        atomicAdd(&s_t[c], ph_signed(PhM<Real>::fixed(t_exit), neg));
-        depth = A::sub(depth, A::mul(rr, t_exit));
-        if (depth < Real(0)) depth = Real(0);
-        // onto the face of axis ax (constant indices only: registers)
-        bool up = false, inside = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == ax) {
-                up = d[a] > Real(0);
-                p[a] = A::mul(Real(ix[a] + (up ? 1 : 0)), h[a]);
-                const int nxt = ix[a] + (up ? 1 : -1);
-                inside = nxt >= 0 && nxt < nc[a];
-                if (inside) ix[a] = nxt;
+                    for (int a = 0; a < 3; ++a)
+                        if (a == ax) d[a] = -d[a];
+                }
+                if (diffuse) ph_lambert<Real>(f, u01<Real>(r.b), u01<Real>(r.c), d);
             }
         }
-        if (inside) {
-            c = (ix[0] * P.ny + ix[1]) * P.nz + ix[2];
-            continue;
-        }
-        // a face of the domain
-        const int f = 2 * ax + (up ? 1 : 0);
-        const int kind = P.face[f];
-        if (kind == PH_ISOTHERMAL) {
-            atomicAdd(&s_out[f], 1ull);
-            active = false;
-            continue;
-        }
-        if (kind == PH_SPECULAR) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (a == ax) d[a] = -d[a];
-            continue;
-        }
-        const U4 r = st.draw();
-        const Real u0 = u01<Real>(r.a);
-        bool diffuse = true;
-        if (kind == PH_INTERFACE) {
-            if (u0 < __ldg(tau12 + b)) {
-                atomicAdd(&s_out[f], 1ull);
-                active = false;
-                continue;
-            }
-        } else if (u0 < Real(P.p_spec[f])) {  // rough: specular part
-            diffuse = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (a == ax) d[a] = -d[a];
-        }
-        if (diffuse) ph_lambert<Real>(f, u01<Real>(r.b), u01<Real>(r.c), d);
     }
     atomicAdd(&s_out[6], n_seg);
     atomicAdd(&s_out[7], n_cap);

@@ -496,6 +496,8 @@ emc_status phonon_run(emc_ctx* ctx, const emc_phonon_config& pc, const PhTables&
     const int block = pc.block_size ? pc.block_size : 256;
     const size_t smem = ph_smem_bytes<Real>(C);
     PCK(cudaFuncSetAttribute(k_phonon<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PCK(cudaFuncSetAttribute(k_phonon<Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared));
     int dev = 0, nsm = 0, occ = 0;
     PCK(cudaGetDevice(&dev));
     PCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -655,9 +655,11 @@ struct StepSums<double> {
 // grid), one particle per lane, with coalesced state loads and stores.  The
 // round robin spreads every stretch of the slot range over all warps, so a
 // sorted range (neighbouring slots in neighbouring subcells, a hot drain end
-// and a cool source end) still balances.  Inside a step every iteration
-// carries the particle to its next event -- the end of the step or a
-// scattering -- through one shared drift and wall check.  Block tallies in
+// and a cool source end) still balances.  Every free flight carries the
+// particle to its next event -- the end of its step or a scattering --
+// through one shared drift and wall check; the lanes of a warp need not be
+// in the same step (the field is fixed within a launch), and scatterings
+// wait until enough lanes have one (below).  Block tallies in
 // shared memory are indexed by ensemble (the first WE ensembles; others go
 // straight to global atomics).  The rate table of a single table set is
 // staged in shared memory for bins [0, nbs); the per-table-set physics for
@@ -724,79 +726,122 @@ __global__ void __launch_bounds__(256, 4)
         // particle hand them over (warp-wide, all lanes converged here)
         const bool need = valid && int(tg >> 8) != S.e;
         if (__any_sync(0xffffffffu, need)) S.flush_warp(P, bt, e_base, need);
-        if (!valid) continue;
         QEntry<Real> Q;
         Part<Real>& q = Q.q;
-        q.e = int(tg >> 8);
-        q.v = int(tg & 0xFFu);
-        S.e = q.e;
-        q.kx = static_cast<const Real*>(P.kx)[p];
-        q.ky = static_cast<const Real*>(P.ky)[p];
-        q.kz = static_cast<const Real*>(P.kz)[p];
-        if (NW) {
-            q.x = static_cast<const Real*>(P.x)[p];
-            q.y = static_cast<const Real*>(P.y)[p];
-            q.z = static_cast<const Real*>(P.z)[p];
-        } else {
-            q.x = q.y = q.z = Real(0);
+        q.e = valid ? int(tg >> 8) : 0;
+        q.v = valid ? int(tg & 0xFFu) : 0;
+        q.kx = q.ky = q.kz = q.x = q.y = q.z = q.tr = q.E = q.f = Real(0);
+        q.ctr = 0;
+        q.id = 0;
+        q.seed = 0;
+        if (valid) {
+            S.e = q.e;
+            q.kx = static_cast<const Real*>(P.kx)[p];
+            q.ky = static_cast<const Real*>(P.ky)[p];
+            q.kz = static_cast<const Real*>(P.kz)[p];
+            if (NW) {
+                q.x = static_cast<const Real*>(P.x)[p];
+                q.y = static_cast<const Real*>(P.y)[p];
+                q.z = static_cast<const Real*>(P.z)[p];
+            }
+            q.tr = static_cast<const Real*>(P.tr)[p];
+            q.ctr = P.ctr[p];
+            q.id = gid_of(P, q.e, P.id[p]);
+            q.seed = P.seed[q.e];
         }
-        q.tr = static_cast<const Real*>(P.tr)[p];
-        q.ctr = P.ctr[p];
-        q.id = gid_of(P, q.e, P.id[p]);
-        q.seed = P.seed[q.e];
         const int ts = P.tabset[q.e];
         const Phys<Real>& ph = (ts < K.n_tab_s) ? ph_s[ts] : ph_g[ts];
         const Real* tab_g = tab_all + (size_t)ts * NV * K.nb * NM;
-        q.E = kane_E(ph.ck[q.v] * norm2(q.kx, q.ky, q.kz), ph.alpha[q.v]);
-        q.f = ph.vk[q.v] / fma_(Real(2) * ph.alpha[q.v], q.E, Real(1));
-        Real f4[4];
-        if (!NW) load4<Real>(static_cast<const Real*>(P.acc_bulk) + 4 * (size_t)q.e, f4);
+        if (valid) {
+            q.E = kane_E(ph.ck[q.v] * norm2(q.kx, q.ky, q.kz), ph.alpha[q.v]);
+            q.f = ph.vk[q.v] / fma_(Real(2) * ph.alpha[q.v], q.E, Real(1));
+        }
+        Real f4[4] = {Real(0), Real(0), Real(0), Real(0)};
         int cell = -1;
-        StepSums<Real> ss;
-        bool live = true;
-        for (int s = 0; s < n_steps && live; ++s) {
+        if (valid) {
             if (NW) {
-                // the field of the subcell at the start of the step (reloaded
+                // the field of the subcell at the start of a step (reloaded
                 // only when the particle has changed subcell)
-                const int c = cell_of<Real>(K, q.x, q.y, q.z);
-                if (c != cell) {
-                    load4<Real>(static_cast<const Real*>(P.acc_cell) + 4 * ((size_t)q.e * K.ncell + c), f4);
-                    cell = c;
-                }
+                cell = cell_of<Real>(K, q.x, q.y, q.z);
+                load4<Real>(static_cast<const Real*>(P.acc_cell) + 4 * ((size_t)q.e * K.ncell + cell), f4);
+            } else {
+                load4<Real>(static_cast<const Real*>(P.acc_bulk) + 4 * (size_t)q.e, f4);
             }
-            Real tleft = dt;
-            for (int it = 0;; ++it) {
+        }
+        StepSums<Real> ss;
+        // The warp runs in step: each round the lanes without a pending
+        // scattering take one free flight (to the end of their step or to
+        // their next scattering, through the walls); the pending scatterings
+        // (mechanism choice, final state) run once at least a third of the
+        // lanes still working wait for one, so that code runs with many
+        // lanes of the warp instead of with the few that scatter in a given
+        // step (a third measured fastest: a half or more leaves too many
+        // lanes idle in the flights, a quarter or less runs the scatterings
+        // with too few).  A particle's own sequence of flights, draws and
+        // tallies is the same as step by step.
+        bool live = true, done = !valid || n_steps <= 0, pending = false;
+        int s = 0, it = 0;
+        Real tleft = dt;
+        for (;;) {
+            if (!done && !pending) {
+                bool step_end = false;
                 if (it >= MAX_FLIGHTS_PER_STEP) {
                     atomicOr(P.err, ERR_FLIGHTS);
-                    break;
-                }
-                const bool step_end = q.tr >= tleft;
-                drift<Real, NW>(q, ph, f4, step_end ? tleft : q.tr);
-                if (NW && walls(q, P, K, bt, e_base)) {
-                    live = false;
-                    break;
+                    step_end = true;  // the step ends where the particle is
+                } else {
+                    ++it;
+                    const bool to_end = q.tr >= tleft;
+                    drift<Real, NW>(q, ph, f4, to_end ? tleft : q.tr);
+                    if (NW && walls(q, P, K, bt, e_base)) {
+                        live = false;
+                        done = true;
+                    } else if (to_end) {
+                        q.tr -= tleft;
+                        step_end = true;
+                    } else {
+                        tleft -= q.tr;
+                        pending = true;
+                    }
                 }
                 if (step_end) {
-                    q.tr -= tleft;
-                    break;
+                    ss.add(S, q.f * q.kx, q.f * q.ky, q.f * q.kz, q.E, q.E + ph.Ec[q.v]);
+                    S.count_valley(q.v);
+                    ++s;
+                    it = 0;
+                    tleft = dt;
+                    if (s >= n_steps) {
+                        done = true;
+                    } else if (NW) {
+                        const int cc = cell_of<Real>(K, q.x, q.y, q.z);
+                        if (cc != cell) {
+                            load4<Real>(static_cast<const Real*>(P.acc_cell) + 4 * ((size_t)q.e * K.ncell + cc), f4);
+                            cell = cc;
+                        }
+                    }
                 }
-                tleft -= q.tr;
+            }
+            const unsigned pend = __ballot_sync(0xffffffffu, pending);
+            const unsigned work = __ballot_sync(0xffffffffu, !done);
+            if (work == 0u) break;
+            if (3 * __popc(pend) < __popc(work)) continue;
+            if (pending) {
                 if (choose<Real>(Q, P, K, ph, tab_s, nbs1, tab_g, bt, e_base) >= 0)
                     final_state<Real, NW>(Q, P, K, ph, bt, e_base);
+                pending = false;
             }
-            if (!live) break;
-            ss.add(S, q.f * q.kx, q.f * q.ky, q.f * q.kz, q.E, q.E + ph.Ec[q.v]);
-            S.count_valley(q.v);
         }
-        ss.fold(S);
-        store<Real>(P, p, q, NW);
-        P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
-        if (NW && !live) {
-            // left through a contact: its id is free for the refill
-            const uint32_t i = P.id[p];
-            atomicOr(&P.dead_bits[P.bits_off[q.e] + (i >> 5)], 1u << (i & 31u));
+        if (valid) {
+            ss.fold(S);
+            store<Real>(P, p, q, NW);
+            P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);
+            if (NW && !live) {
+                // left through a contact: its id is free for the refill
+                const uint32_t i = P.id[p];
+                atomicOr(&P.dead_bits[P.bits_off[q.e] + (i >> 5)], 1u << (i & 31u));
+            }
         }
-        if (NW && count_charge && live) agg_add_i(P.charge, q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z));
+        if (NW && count_charge && valid && live)
+            agg_add_i(P.charge, q.e * K.ncell + cell_of<Real>(K, q.x, q.y, q.z));
     }
     S.flush_warp(P, bt, e_base, true);
     __syncthreads();

@@ -489,6 +489,11 @@ def phonon_comparison(args, stream) -> dict:
         r = emc.emc.phonon_solve(ctx, tc, pc, q, N)
         mc = ET.phonon_mc_temperature(ctx, tc, pc, q, N, passes=3, first=N)
         T_f, _ = emc.emc.thermal_solve(ctx, tc_f, q[None, :])
+        # the coupled fixed points from 300 K: electrons <-> phonon Monte
+        # Carlo, and electrons <-> Fourier (the same electron windows)
+        T0 = np.full((1, ctx.n_cell), 300.0)
+        hy = ET.hybrid_iterate(ctx, tc, pc, T0, args.phonon_loop_bundles, max_iter=10, first=10 * N)
+        fo = ET.iterate(ctx, tc_f, T0, max_iter=10)
     finally:
         ctx.close()
     P = r["power_W"]
@@ -507,6 +512,17 @@ def phonon_comparison(args, stream) -> dict:
         "heat_net_W": net, "heat_abs_W": P,
         "peak_rise_K": {"phonon_mc": peak_mc, "fourier": peak_f, "mc_passes": mc["peak_history"]},
         "R_th_K_per_W_half_wire": {"phonon_mc": peak_mc / net, "fourier": peak_f / net},
+        "coupled_fixed_point": {
+            "what": "electron MC <-> phonon MC and electron MC <-> Fourier from 300 K (300 + 1000 steps per "
+                    "iteration, %d bundles per phonon solve); stop: every subcell within max(0.1 K, the noise)"
+                    % args.phonon_loop_bundles,
+            "phonon_mc": {"converged": bool(hy["converged"]), "iterations": int(hy["iterations"]),
+                          "seconds": round(hy["seconds"], 3), "peak_rise_K": [round(float(x[0]), 2) for x in hy["history"]],
+                          "R_th_K_per_W_half_wire": float(hy["R_th_K_per_W"][0])},
+            "fourier": {"converged": bool(fo["converged"]), "iterations": int(fo["iterations"]),
+                        "seconds": round(fo["seconds"], 3), "peak_rise_K": [round(float(x[0]), 2) for x in fo["history"]],
+                        "R_th_K_per_W_half_wire": float(fo["R_th_K_per_W"][0])},
+        },
         "rise_along_x_K": {"phonon_mc": (mc["T"].reshape(cfg["nx"], nyz).mean(axis=1) - 300.0)[::10].round(2).tolist(),
                            "fourier": (T_f[0].reshape(cfg["nx"], nyz).mean(axis=1) - 300.0)[::10].round(2).tolist(),
                            "x_um": [round((i + 0.5) / cfg["nx"] * cfg["Lx"] * 1e6, 3) for i in range(0, cfg["nx"], 10)]},
@@ -780,6 +796,7 @@ def main():
     ap.add_argument("--no-phonon", action="store_true", help="skip the phonon Monte Carlo of the 20 V wire")
     ap.add_argument("--phonon-bundles", type=int, default=10_000_000)
     ap.add_argument("--phonon-cpu-bundles", type=int, default=4_000_000)
+    ap.add_argument("--phonon-loop-bundles", type=int, default=2_000_000)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
     ap.add_argument("--et-judge-steps", type=int, default=5000)

@@ -132,6 +132,45 @@ def iterate(ctx, tc, T0: np.ndarray, warm_steps: int = 300, avg_steps: int = 100
     return _result(ctx, tc, T, q, max_iter, False, hist, d_hist, n_hist, t0)
 
 
+def hybrid_iterate(ctx, tc, pc, T0: np.ndarray, n_bundles: int, warm_steps: int = 300, avg_steps: int = 1000,
+                   max_iter: int = 15, stop_K: float = 0.1, first: int = 0) -> dict:
+    """Electron Monte Carlo <-> phonon Monte Carlo fixed point from T0 (the
+    hybrid method with the phonon side in the transistor region): each
+    iteration takes the electrons' heat map at the current subcell
+    temperatures, and the phonon Monte Carlo (emc_phonon_solve, rates at the
+    current temperatures) gives the next ones, for every ensemble of the
+    context.  The stop test is _stop, with the noise of both Monte Carlos:
+    the two half-window heat maps each carried by their own bundles."""
+    T = np.array(T0, dtype=float)
+    hist, d_hist, n_hist = [], [], []
+    t0 = time.perf_counter()
+    q = None
+    nxt = first
+
+    def phonon_T(heat, Tc):
+        nonlocal nxt
+        out = np.empty_like(Tc)
+        for e in range(ctx.n_ens):
+            r = _emc.phonon_solve(ctx, tc, pc, heat[e], n_bundles, T_cells=Tc[e], first=nxt)
+            nxt += n_bundles
+            out[e] = tc.T_sink + r["dT"]
+        return out
+
+    for it in range(1, max_iter + 1):
+        q, qa, qb = mc_heat_halves(ctx, T, warm_steps, avg_steps)
+        Tn = phonon_T(q, T)
+        Ta = phonon_T(qa, T)
+        Tb = phonon_T(qb, T)
+        ok, d, n = _stop(Tn, T, Ta, Tb, stop_K)
+        T = Tn
+        hist.append(peak_rise(T, tc.T_sink))
+        d_hist.append(float(d.max()))
+        n_hist.append(float(n.max()))
+        if ok and it > 1:
+            return _result(ctx, tc, T, q, it, True, hist, d_hist, n_hist, t0)
+    return _result(ctx, tc, T, q, max_iter, False, hist, d_hist, n_hist, t0)
+
+
 def judge(ctx, tc, T: np.ndarray, warm_steps: int = 300, avg_steps: int = 5000) -> dict:
     """The plain Monte Carlo's verdict on a temperature field: one long
     Monte Carlo window at the subcell temperatures T, then the Fourier solve

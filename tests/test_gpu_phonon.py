@@ -167,3 +167,22 @@ def test_phonon_solve_rejects_bad_input(emc):
     with emc.Context(W.bulk(n_particles=100)) as ctx:
         with pytest.raises(emc.EmcError):
             emc.emc.phonon_solve(ctx, tc, emc.emc.phonon_config(), np.ones(1), 10)
+
+
+def test_electron_phonon_monte_carlo_loop_converges(emc):
+    """The hybrid loop with the phonon side in the transistor region
+    (electrothermal.hybrid_iterate): from 300 K it reaches a fixed point
+    within the Monte Carlo noise and heats the wire; its last two iterates'
+    peak rises agree within that noise."""
+    from paper_1707_09073_gb300 import electrothermal as ET
+    cfg = W.nanowire(n_particles=40_000, nx=20, Lx=200e-9, Vd=4.0, seed=33)
+    tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC, n_e=cfg["Nd"], elec=W.ELECTRON_PHONON_GAN)
+    pc = emc.emc.phonon_config(emc.emc.WIRE_FACES, n_bins=500, precision=emc.FP32, seed=5)
+    with emc.Context(cfg) as ctx:
+        ET.warm_to_steady(ctx)
+        T0 = np.full((1, ctx.n_cell), 300.0)
+        r = ET.hybrid_iterate(ctx, tc, pc, T0, 400_000, max_iter=10)
+        assert r["converged"], (r["history"], r["max_dT_K"], r["noise_K"])
+        assert r["peak"][0] > 1.0 and np.isfinite(r["R_th_K_per_W"][0])
+        h = r["history"]
+        assert abs(h[-1][0] - h[-2][0]) <= max(0.1, r["noise_K"][-1]) + 1e-9, (h, r["noise_K"])

@@ -115,3 +115,40 @@ def test_thermal_solve_with_interface_of_eqs_2_and_3(emc):
                           area_ratio=ratio)
         np.testing.assert_allclose(T[0] - 300.0, want - 300.0, rtol=1e-5)
         assert (T[0] > 300.0).all()
+
+
+def test_thermal_resistance_chain_matches_oracle(emc, oracle_mod):
+    """R_th of the Fig. 5 definition through the library (FP64 electron Monte
+    Carlo -> net phonon energy per subcell (EMC_TALLY_HEAT_J) -> Fourier
+    solve with the GaN/SiC interface of Eqs. (2)-(3) -> peak rise over the
+    emitted power) against the same chain through the oracle (its per-cell
+    event counts -> net phonon energy -> oracle/thermal.solve): the electron
+    runs give the same events, the two thermal solves agree to 1e-5."""
+    from oracle import thermal as tref
+    from emc_harness import oracle_heat
+    from paper_1707_09073_gb300 import electrothermal as ET
+    cfg = W.nanowire(n_particles=6000, nx=20, Lx=200e-9, Vd=4.0, seed=7)
+    steps = 60
+    ref = oracle_mod.Sim(cfg)
+    ref.run(steps)
+    rt = ref.tallies()
+    Vc = cfg["Lx"] * cfg["Ly"] * cfg["Lz"] / (cfg["nx"] * cfg["ny"] * cfg["nz"])
+    window = steps * cfg["dt"]
+    tc = emc.emc.thermal_config(W.TABLE_II_GAN, h_bottom=0.0, L_boundary=120e-9, tol_K=1e-9,
+                                substrate=W.TABLE_II_SIC, area_ratio=10.0)
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        q_lib = ET.heat_map(ctx, window)
+        T_lib, _ = emc.emc.thermal_solve(ctx, tc, q_lib)
+        P_lib = ET.emitted_power(ctx, q_lib)
+        R_lib = ET.thermal_resistance(T_lib, P_lib, 300.0)[0]
+    w = cfg["Nd"] * cfg["Lx"] * cfg["Ly"] * cfg["Lz"] / cfg["n_particles"]
+    h = oracle_heat(rt["events"])
+    J = (h[:, 0] * cfg["hw_lo_eV"] + h[:, 1] * cfg["hw_iv_eV"]) * 1.602176634e-19 * w
+    q_orc = J / (window * Vc)
+    np.testing.assert_allclose(q_lib[0], q_orc, rtol=1e-12, atol=1e-12 * np.abs(q_orc).max())
+    T_orc = tref.solve(cfg, q_orc, W.TABLE_II_GAN, h_bottom=0.0, L_b=120e-9, tol=1e-9, substrate=W.TABLE_II_SIC,
+                       area_ratio=10.0)
+    R_orc = (T_orc.max() - 300.0) / (q_orc.sum() * Vc)
+    assert P_lib[0] > 0 and R_orc > 0
+    assert abs(R_lib / R_orc - 1) < 1e-5, (R_lib, R_orc)

@@ -378,6 +378,10 @@ emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, f
  * set (src != NULL, applied after the get). */
 emc_status emc_mlp_params(emc_mlp* m, float* dst, const float* src, int64_t* count);
 const char* emc_mlp_last_error(const emc_mlp* m);
+/* Diagnostic: set the handle's device error word as an expired tensor-core
+ * wait sets it, so that the next call that checks it returns EMC_ETIMEOUT
+ * (and clears it); lets the reporting path be tested without an expiry. */
+emc_status emc_mlp_debug_set_error(emc_mlp* m);
 void emc_mlp_destroy(emc_mlp* m);
 
 /* The surrogate attached to a Monte Carlo context (the learned part's calls

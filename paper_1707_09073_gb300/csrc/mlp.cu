@@ -667,6 +667,15 @@ emc_status emc_mlp_create(const emc_mlp_config* cfg, void* stream, emc_mlp** out
     return EMC_OK;
 }
 
+emc_status emc_mlp_debug_set_error(emc_mlp* m)
+{
+    if (!m) return EMC_EINVAL;
+    const int one = 1;
+    MCK(cudaMemcpyAsync(m->d_err, &one, sizeof(int), cudaMemcpyHostToDevice, m->st));
+    MCK(cudaStreamSynchronize(m->st));
+    return EMC_OK;
+}
+
 emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n)
 {
     if (!m || (n > 0 && (!X || !Y)) || n < 0) return EMC_EINVAL;

@@ -145,3 +145,18 @@ def test_surrogate_on_the_context_equals_the_standalone_network(emc):
         assert p1.size == p2.size and np.linalg.norm(p2 - p1) <= 1e-3 * np.linalg.norm(p1)
         y1, y2 = net.infer(X[:300]), ctx.emc_surrogate_infer(X[:300])
         assert y2.shape == y1.shape and np.abs(y2 - y1).max() <= 1e-2 * np.abs(y1).max()
+
+
+def test_expired_wait_is_reported_and_the_handle_recovers(emc):
+    """The reporting path of an expired tensor-core wait: with the device
+    error word set (as the bounded mbarrier wait sets it; no wait is made to
+    expire), the next call returns EMC_ETIMEOUT with its message, and the
+    call after it runs normally with the same results."""
+    net, nrm, sizes, rng = make(emc)
+    X = rng.normal(size=(300, 4)).astype(np.float32)
+    want = net.infer(X)
+    net.debug_set_error()
+    with pytest.raises(emc.EmcError) as ei:
+        net.infer(X)
+    assert ei.value.status == 5 and "expired" in str(ei.value)
+    np.testing.assert_array_equal(net.infer(X), want)

@@ -151,3 +151,43 @@ def test_shard_protocol_errors(emc):
         q, f = ctx.emc_shard_counts()
         with pytest.raises(emc.EmcError):  # prefix above the total
             ctx.emc_shard_tail(q, f + 1, f, True)
+
+
+def test_sharded_wire_with_subcell_temperatures_and_resume(emc):
+    """Shards under per-subcell lattice temperatures (set between periods,
+    as the electrothermal loop does) follow the unsharded run bit for bit,
+    and a checkpoint of every shard taken after an exchange resumes into
+    fresh shard contexts with the same continuation (FP64)."""
+    cfg = W.nanowire(n_particles=8000, nx=20, Lx=200e-9, Vd=5.0, seed=61)
+    K = cfg["steps_per_poisson"]
+    C = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    T = 300.0 + 60.0 * np.linspace(0.0, 1.0, C)
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(3 * K)
+        ctx.emc_set_temperature(0, T)
+        ctx.emc_step(6 * K)
+        want = _wire_tallies(emc, ctx)
+        want_p = _particles_by_gid(emc, ctx, [cfg])
+    with SH.LocalWire(cfg, 2, precision=emc.FP64) as wire:
+        wire.emc_step(3 * K)
+        for c in wire.ctxs:
+            c.emc_set_temperature(0, T)
+        wire.emc_step(3 * K)
+        blobs = [c.emc_get_state() for c in wire.ctxs]
+        wire.emc_step(3 * K)
+        got = _wire_tallies(emc, wire)
+        got_p = {}
+        for c in wire.ctxs:
+            got_p.update(_particles_by_gid(emc, c, c.cfgs))
+    _assert_same(got, want)
+    assert got_p == want_p
+    # resume the checkpoint into fresh shards and finish the same steps
+    with SH.LocalWire(cfg, 2, precision=emc.FP64) as wire:
+        for c, b in zip(wire.ctxs, blobs):  # the blob carries the temperature tables
+            c.emc_set_state(b)
+        wire.steps = 6 * K
+        wire.emc_step(3 * K)
+        res_p = {}
+        for c in wire.ctxs:
+            res_p.update(_particles_by_gid(emc, c, c.cfgs))
+    assert res_p == want_p

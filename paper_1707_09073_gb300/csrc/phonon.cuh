@@ -291,8 +291,16 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
         if (live == 0u) break;
         if (2 * __popc(pend) < __popc(live)) continue;
         // the pending events
+        // the lanes that want a new bundle take consecutive ids with one
+        // atomic per warp
+        const unsigned want = __ballot_sync(0xFFFFFFFFu, !done && ev == 3);
+        unsigned long long base = 0ull;
+        if (want) {
+            if ((threadIdx.x & 31) == __ffs(want) - 1) base = atomicAdd(P.next, (unsigned long long)__popc(want));
+            base = __shfl_sync(0xFFFFFFFFu, base, __ffs(want) - 1);
+        }
         if (!done && ev == 3) {
-            const unsigned long long i = atomicAdd(P.next, 1ull);
+            const unsigned long long i = base + __popc(want & ((1u << (threadIdx.x & 31)) - 1u));
             if (i >= (unsigned long long)P.n_bundles) {
                 done = true;
             } else {

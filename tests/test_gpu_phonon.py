@@ -186,3 +186,44 @@ def test_electron_phonon_monte_carlo_loop_converges(emc):
         assert r["peak"][0] > 1.0 and np.isfinite(r["R_th_K_per_W"][0])
         h = r["history"]
         assert abs(h[-1][0] - h[-2][0]) <= max(0.1, r["noise_K"][-1]) + 1e-9, (h, r["noise_K"])
+
+
+def test_full_size_wire_sampled_bundles_and_bookkeeping(emc):
+    """The benchmarked phonon problem at its full size (the 1 um wire, 3 x 6 x
+    100 subcells, 1000 bins, 10^7 bundles, FP32): every bundle ends at a
+    face, the bundles start in the subcells in proportion to |q| (multinomial,
+    5 sigma); and a sample of the same bundle ids (20,000 from the middle of
+    the range) in the parity build follows the oracle: the same emissions,
+    and scatterings, face counts and residence times within what rounding
+    alone produces on paths this long (227 segments per bundle through
+    mirrors and faces): one-ulp differences grow along a path, and the oracle
+    built with and without fused multiply-adds differs in the scattering
+    counts of 364 of the 1800 subcells (by at most 5), in one face count by 1
+    and in the segment count by 8e-5."""
+    cfg = W.nanowire(n_particles=10, Vd=20.0, seed=1)
+    C = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    x = (np.arange(cfg["nx"]) + 0.5) / cfg["nx"]
+    q = np.repeat(1.0 + 8.0 * np.exp(-((x - 0.75) / 0.08) ** 2), cfg["ny"] * cfg["nz"]) * 1e17
+    q[: 5 * cfg["ny"] * cfg["nz"]] *= -0.2
+    tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC)
+    N = 10_000_000
+    with emc.Context(cfg) as ctx:
+        g = emc.emc.phonon_solve(ctx, tc, emc.emc.phonon_config(n_bins=1000, seed=77), q, N)
+        s = emc.emc.phonon_solve(ctx, tc, emc.emc.phonon_config(n_bins=1000, seed=77, precision=emc.FP64), q,
+                                 20_000, first=5_000_000)
+    assert g["capped"] == 0 and int(g["absorbed"].sum()) == N
+    p = np.abs(q) / np.abs(q).sum()
+    z = (g["emitted"] - N * p) / np.sqrt(N * p * (1 - p))
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    r = PH.solve(cfg, q, GAN, emc.emc.WIRE_FACES, 20_000, seed=77, nb=1000, substrate=SIC, first=5_000_000,
+                 threads=8)
+    assert np.array_equal(s["emitted"], r["emitted"])
+    ds = s["scatterings"].astype(np.int64) - r["scatterings"].astype(np.int64)
+    assert np.abs(ds).max() <= 10 and np.count_nonzero(ds) <= 0.4 * C, (np.count_nonzero(ds), np.abs(ds).max())
+    assert abs(int(s["scatterings"].sum()) / int(r["scatterings"].sum()) - 1) < 2e-3
+    assert np.abs(s["absorbed"].astype(np.int64) - r["absorbed"].astype(np.int64)).max() <= 20
+    assert abs(s["segments"] / r["segments"] - 1) < 1e-3
+    assert abs(s["t_res_ps"].sum() / r["t_res_ps"].sum() - 1) < 1e-3
+    np.testing.assert_allclose(s["dT"].reshape(cfg["nx"], -1).mean(axis=1),
+                               r["dT"].reshape(cfg["nx"], -1).mean(axis=1), rtol=1e-2,
+                               atol=1e-2 * np.abs(r["dT"]).max())

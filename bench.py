@@ -381,44 +381,63 @@ def batched_mixed(args, stream) -> dict:
     """Throughput on the 256-ensemble mixed batch (N ~ 10^U(4, 6), |E| ~
     U(0, 400) kV/cm, T ~ U(300, 600) K, N_d ~ 10^U(16, 19) cm^-3, 192 bulk +
     64 nanowire, 5.5e7 electrons): one context per geometry on the bench
-    stream, one step = 10 fs of every ensemble, CUDA-event timed."""
+    stream, one flight launch per context and Poisson period (profiled for
+    the roofline); one step = 10 fs of every ensemble, CUDA-event timed.
+    The same batch with both contexts in one flight launch per period
+    (emc_group_step) is timed too."""
     import torch
     import paper_1707_09073_gb300 as emc
     cfgs = W.config_batched()
     groups = W.by_geometry(cfgs)
     ctxs = [emc.Context([cfgs[i] for i in idx], stream=stream.cuda_stream) for _, idx in sorted(groups.items())]
-    try:
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                for ctx in ctxs:
-                    ctx.emc_step(STEPS_PER_POISSON)
-            for ctx in ctxs:
-                ctx.emc_tally(emc.TALLY_OBS, reset=True)
+
+    def window(step_fn, profile=False):
+        for ctx in ctxs:
+            ctx.emc_tally(emc.TALLY_OBS, reset=True)
+            ctx.emc_tally(emc.TALLY_EVENTS, reset=True)
+            if profile:
                 ctx.emc_profile(True)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            for _ in range(args.batched_steps):
-                for ctx in ctxs:
-                    ctx.emc_step(STEPS_PER_POISSON)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.batched_steps):
+            step_fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
             prof = [ctx.emc_profile_read() for ctx in ctxs]
             for ctx in ctxs:
                 ctx.emc_profile(False)
-            real = sum(int(ctx.emc_tally(emc.TALLY_EVENTS).sum()) for ctx in ctxs)
-            obs = [o for ctx in ctxs for o in ctx.emc_tally(emc.TALLY_OBS, reset=True)]
+        real = sum(int(ctx.emc_tally(emc.TALLY_EVENTS).sum()) for ctx in ctxs)
+        obs = [o for ctx in ctxs for o in ctx.emc_tally(emc.TALLY_OBS)]
+        return a.elapsed_time(b), real, obs, prof
+
+    def group():
+        emc.emc.group_step(ctxs, STEPS_PER_POISSON)
+
+    def separate():
+        for ctx in ctxs:
+            ctx.emc_step(STEPS_PER_POISSON)
+
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                separate()
+            ms, real, obs, prof = window(separate, profile=True)
+            ms_grp, real_grp, _, _ = window(group)
             # end to end: every step's observables of every ensemble read
             # back into page-locked host buffers (double-buffered)
             bufs = [[ctx.pinned_tally(emc.TALLY_OBS) for ctx in ctxs] for _ in range(2)]
             done = [torch.cuda.Event() for _ in range(2)]
+            for ctx in ctxs:
+                ctx.emc_tally(emc.TALLY_EVENTS, reset=True)
             torch.cuda.synchronize()
             w0 = time.perf_counter()
             for i in range(args.batched_steps):
+                separate()
                 for ctx, ob in zip(ctxs, bufs[i % 2]):
-                    ctx.emc_step(STEPS_PER_POISSON)
                     ctx.emc_tally_async(emc.TALLY_OBS, ob)
                 done[i % 2].record(stream)
                 if i > 0:
@@ -440,10 +459,14 @@ def batched_mixed(args, stream) -> dict:
     return {
         "workload": "256 independent ensembles: N ~ 10^U(4,6) (sum %d), |E| ~ U(0,400) kV/cm, T ~ U(300,600) K, "
                     "N_d ~ 10^U(16,19) cm^-3; 192 bulk (field along c) + 64 half nanowires (V_d = |E| x 1 um, "
-                    "Poisson every 10 fs); one context per geometry" % sum(c["n_particles"] for c in cfgs),
+                    "Poisson every 10 fs); one context per geometry, one flight launch per context per 10 fs"
+                    % sum(c["n_particles"] for c in cfgs),
         "steps": args.batched_steps, "ms_per_step": ms / args.batched_steps,
         "events_per_s": real / (ms * 1e-3), "events_incl_self_per_s": (real + selfe) / (ms * 1e-3),
         "particle_steps_per_s": psteps / (ms * 1e-3),
+        "one_launch_for_both": {"ms_per_step": ms_grp / args.batched_steps,
+                                "events_per_s": real_grp / (ms_grp * 1e-3),
+                                "path": "emc_group_step: both contexts' flights in one launch, blocks split by slots"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
                      "kernel": "k_flight<float, bulk> and k_flight<float, nanowire> (one launch per context and step)",
@@ -451,7 +474,8 @@ def batched_mixed(args, stream) -> dict:
                      "basis": "the op model of the headline roofline over the CUDA-event time of the flight launches"},
         "e2e": {"value": real2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                 "steps": args.batched_steps,
-                "path": "emc_step + emc_tally_async OBS of every ensemble into pinned host buffers, double-buffered"},
+                "path": "emc_step of each context + emc_tally_async OBS of every ensemble into pinned host "
+                        "buffers, double-buffered"},
     }
 
 

@@ -257,6 +257,19 @@ emc_status emc_state_size(emc_ctx* ctx, size_t* bytes);
 emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes);
 emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes);
 
+/* Advance n_ctx (1 or 2) contexts by n_steps time steps together: per chunk
+ * one flight launch covers the particles of both (each context on its own
+ * blocks of the launch, in proportion to its particle slots), then each
+ * nanowire context's contact refill and Poisson update, each context's
+ * sort when due; the result is that of emc_step on each (the mixed bulk +
+ * nanowire batch, which needs one context per geometry, runs as one launch
+ * per chunk).  The chunk is the nanowire contexts' Poisson period (two
+ * nanowire contexts need the same period and phase), else the first
+ * context's steps_per_launch.  The contexts need the same stream, precision
+ * and block size; sharded contexts, and contexts with flight profiling on,
+ * step alone.  The one flight launch per chunk is counted on ctxs[0]. */
+emc_status emc_group_step(emc_ctx* const* ctxs, int32_t n_ctx, int32_t n_steps);
+
 /* One wire's particles sharded over several contexts (the charge exchange
  * of the Poisson passage: the field of a period follows from the electron
  * count of every subcell, summed over all particles of the wire).  Each

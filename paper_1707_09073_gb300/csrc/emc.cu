@@ -22,6 +22,11 @@ template <typename Real> void launch_flight(const DevParams&, bool, int, int, in
 template <typename Real> void launch_init(const DevParams&, bool, cudaStream_t);
 template <typename Real> void launch_inject(const DevParams&, cudaStream_t);
 template <typename Real> void launch_free_counts(const DevParams&, long long*, cudaStream_t);
+template <typename Real>
+cudaError_t pair_prepare(const DevParams&, bool, const DevParams&, bool, int, size_t*, int*);
+template <typename Real>
+void launch_flight_pair(const DevParams&, bool, int, int, const DevParams&, bool, int, int, int, int, size_t,
+                        cudaStream_t);
 template <typename Real> cudaError_t flight_set_smem(size_t);
 template <typename Real> size_t flight_smem_bytes(int, int);
 template <typename Real> int flight_blocks_per_sm(bool, int, size_t);
@@ -1253,6 +1258,64 @@ emc_status step_impl(emc_ctx* ctx, int32_t n)
     return EMC_OK;
 }
 
+// Two contexts advanced together: per chunk one flight launch over both
+// contexts' particles (each on its own blocks), then each nanowire
+// context's refill and Poisson update, each context's sort when due.  The
+// chunk is the nanowire contexts' Poisson period (both in phase when both
+// are nanowire), else the first context's steps per launch.
+template <typename Real>
+emc_status pair_step_impl(emc_ctx* a, emc_ctx* b, int32_t n)
+{
+    emc_ctx* ctx = a;  // errors are reported on the first context
+    emc_ctx* c2[2] = {a, b};
+    const bool nw[2] = {a->geom == EMC_GEOM_NANOWIRE, b->geom == EMC_GEOM_NANOWIRE};
+    const int block = a->block;
+    size_t smem = 0;
+    int bps = 0;
+    CK(pair_prepare<Real>(a->P, nw[0], b->P, nw[1], block, &smem, &bps));
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t tiles = (a->n_slots + block - 1) / block + (b->n_slots + block - 1) / block;
+    const int64_t cap = (int64_t)nsm * (bps > 0 ? bps : 1);
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    while (n > 0) {
+        int chunk = std::min(n, a->spl);
+        for (int i = 0; i < 2; ++i)
+            if (nw[i]) {
+                const int into = int(c2[i]->steps_done % c2[i]->K);
+                chunk = std::min(n, c2[i]->K - into);
+            }
+        bool boundary[2] = {false, false};
+        for (int i = 0; i < 2; ++i)
+            if (nw[i]) {
+                boundary[i] = (c2[i]->steps_done % c2[i]->K) + chunk == c2[i]->K;
+                if (boundary[i])
+                    CK(cudaMemsetAsync(c2[i]->charge, 0, sizeof(int) * (size_t)c2[i]->n_ens * c2[i]->ncell, a->st));
+            }
+        launch_flight_pair<Real>(a->P, nw[0], chunk, boundary[0] ? 1 : 0, b->P, nw[1], chunk, boundary[1] ? 1 : 0,
+                                 block, grid, smem, a->st);
+        a->launches += 1;  // one launch for both contexts
+        CK(cudaGetLastError());
+        for (int i = 0; i < 2; ++i) {
+            emc_ctx* c = c2[i];
+            if (boundary[i]) {
+                emc_status s = chunk_tail<Real>(c);
+                if (s != EMC_OK) return s;
+            }
+            c->steps_done += chunk;
+            if (c->sort_period > 0 && ++c->flights_since_sort >= c->sort_period && (!nw[i] || boundary[i])) {
+                emc_status s = sort_particles<Real>(c);
+                if (s != EMC_OK) return s;
+                c->flights_since_sort = 0;
+            }
+        }
+        CK(cudaGetLastError());
+        n -= chunk;
+    }
+    return EMC_OK;
+}
+
 template <typename Real>
 emc_status shard_tail_impl(emc_ctx* ctx)
 {
@@ -1887,6 +1950,26 @@ emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_lau
     if (flight_ms) *flight_ms = tot;
     if (flight_launches) *flight_launches = (int64_t)(ctx->ev_used / 2);
     return EMC_OK;
+}
+
+emc_status emc_group_step(emc_ctx* const* ctxs, int32_t n_ctx, int32_t n_steps)
+{
+    if (!ctxs || n_ctx < 1 || n_ctx > 2) return EMC_EINVAL;
+    for (int i = 0; i < n_ctx; ++i)
+        if (!ctxs[i]) return EMC_EINVAL;
+    if (n_ctx == 1) return emc_step(ctxs[0], n_steps);
+    emc_ctx *a = ctxs[0], *b = ctxs[1];
+    if (a == b) return fail(a, EMC_EINVAL, "emc_group_step: the same context twice");
+    if (n_steps < 0) return fail(a, EMC_EINVAL, "n_steps < 0");
+    if (n_steps == 0) return EMC_OK;
+    if (a->st != b->st || a->prec != b->prec || a->block != b->block)
+        return fail(a, EMC_EINVAL, "emc_group_step: the contexts need one stream, precision and block size");
+    if (a->sharded || b->sharded) return fail(a, EMC_EINVAL, "emc_group_step: sharded contexts step alone");
+    if (a->geom == EMC_GEOM_NANOWIRE && b->geom == EMC_GEOM_NANOWIRE &&
+        (a->K != b->K || a->steps_done % a->K != b->steps_done % b->K))
+        return fail(a, EMC_EINVAL, "emc_group_step: nanowire contexts need the same Poisson period and phase");
+    if (a->prof || b->prof) return fail(a, EMC_EINVAL, "emc_group_step: flight profiling is per context");
+    return a->prec == EMC_FP64 ? pair_step_impl<double>(a, b, n_steps) : pair_step_impl<float>(a, b, n_steps);
 }
 
 emc_status emc_shard_counts(emc_ctx* ctx, int32_t* charge_out, int64_t* free_out)

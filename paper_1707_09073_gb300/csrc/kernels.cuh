@@ -687,11 +687,13 @@ __device__ __forceinline__ void flush_window(const DevParams& P, BlockTally* bt)
     }
 }
 
+// The flight of one context's particles by the blocks blk = 0 .. nblk - 1 of
+// a launch (a launch may run two contexts side by side, each on its own
+// blocks: k_flight_pair).
 template <typename Real, bool NW>
-__global__ void __launch_bounds__(256, 4)
-    k_flight(const DevParams P, const KConst<Real> K, int n_steps, int count_charge)
+__device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Real>& K, int n_steps, int count_charge,
+                                            unsigned char* sm, int blk, int nblk)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
     const int nbs = K.nbs;
     Real* tab_s = reinterpret_cast<Real*>(sm);
     size_t off = ((size_t)NV * nbs * NM * sizeof(Real) + 15) & ~size_t(15);
@@ -715,10 +717,10 @@ __global__ void __launch_bounds__(256, 4)
     const int nbs1 = (K.n_tab == 1) ? nbs : 0;
     const int e_base = 0;
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t warps = (int64_t)nblk * (blockDim.x >> 5);
     const int64_t n_chunks = (P.n_slots + 31) >> 5;
     Samples<Real> S;
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+    for (int64_t c = (int64_t)blk * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
         const int64_t p = c * 32 + lane;
         const uint32_t tg = (p < P.n_slots) ? P.tag[p] : uint32_t(DEAD);
         const bool valid = (tg & 0xFFu) != DEAD;
@@ -846,6 +848,28 @@ __global__ void __launch_bounds__(256, 4)
     S.flush_warp(P, bt, e_base, true);
     __syncthreads();
     flush_window(P, bt);
+}
+
+template <typename Real, bool NW>
+__global__ void __launch_bounds__(256, 4)
+    k_flight(const DevParams P, const KConst<Real> K, int n_steps, int count_charge)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    flight_body<Real, NW>(P, K, n_steps, count_charge, sm, blockIdx.x, gridDim.x);
+}
+
+// Two contexts in one launch: blocks [0, nblk0) fly context 0, the others
+// context 1 (the mixed bulk + nanowire batch: one context per geometry).
+template <typename Real, bool NW0, bool NW1>
+__global__ void __launch_bounds__(256, 4)
+    k_flight_pair(const DevParams P0, const KConst<Real> K0, int n_steps0, int count0, const DevParams P1,
+                  const KConst<Real> K1, int n_steps1, int count1, int nblk0)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    if ((int)blockIdx.x < nblk0)
+        flight_body<Real, NW0>(P0, K0, n_steps0, count0, sm, blockIdx.x, nblk0);
+    else
+        flight_body<Real, NW1>(P1, K1, n_steps1, count1, sm, (int)blockIdx.x - nblk0, (int)gridDim.x - nblk0);
 }
 
 // ---------------------------------------------------------------- init
@@ -1234,10 +1258,8 @@ int flight_blocks_per_sm(bool nw, int block, size_t smem)
 }
 
 template <typename Real>
-void launch_flight(const DevParams& P, bool nw, int n_steps, int count_charge, int block, int grid_cap,
-                   cudaStream_t st)
+KConst<Real> flight_consts(const DevParams& P)
 {
-    if (P.n_slots <= 0) return;
     KConst<Real> K;
     K.Lx = Real(P.Lx);
     K.Ly = Real(P.Ly);
@@ -1256,14 +1278,60 @@ void launch_flight(const DevParams& P, bool nw, int n_steps, int count_charge, i
     K.nbs = P.nb_smem;
     K.n_tab = P.n_tab;
     K.n_tab_s = P.n_tab <= 64 ? P.n_tab : 0;
+    K.per_block = 0;
+    return K;
+}
+
+template <typename Real>
+void launch_flight(const DevParams& P, bool nw, int n_steps, int count_charge, int block, int grid_cap,
+                   cudaStream_t st)
+{
+    if (P.n_slots <= 0) return;
+    const KConst<Real> K = flight_consts<Real>(P);
     const int64_t tiles = (P.n_slots + block - 1) / block;
     const int64_t g = tiles < grid_cap ? tiles : grid_cap;
-    K.per_block = 0;
     const size_t smem = flight_smem_bytes<Real>(K.nbs, K.n_tab_s);
     if (nw)
         k_flight<Real, true><<<(unsigned)g, block, smem, st>>>(P, K, n_steps, count_charge);
     else
         k_flight<Real, false><<<(unsigned)g, block, smem, st>>>(P, K, n_steps, count_charge);
+}
+
+// Shared memory and resident blocks per SM of the two-context launch.
+template <typename Real>
+cudaError_t pair_prepare(const DevParams& P0, bool nw0, const DevParams& P1, bool nw1, int block, size_t* smem,
+                         int* blocks_per_sm)
+{
+    const KConst<Real> K0 = flight_consts<Real>(P0), K1 = flight_consts<Real>(P1);
+    const size_t s0 = flight_smem_bytes<Real>(K0.nbs, K0.n_tab_s), s1 = flight_smem_bytes<Real>(K1.nbs, K1.n_tab_s);
+    *smem = s0 > s1 ? s0 : s1;
+    const void* fn = nw0 ? (nw1 ? (const void*)k_flight_pair<Real, true, true> : (const void*)k_flight_pair<Real, true, false>)
+                         : (nw1 ? (const void*)k_flight_pair<Real, false, true> : (const void*)k_flight_pair<Real, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return e;
+    *blocks_per_sm = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, *smem);
+}
+
+// Both contexts in one launch of `grid` blocks, split in proportion to
+// their particle slots (at least one block each).
+template <typename Real>
+void launch_flight_pair(const DevParams& P0, bool nw0, int n_steps0, int count0, const DevParams& P1, bool nw1,
+                        int n_steps1, int count1, int block, int grid, size_t smem, cudaStream_t st)
+{
+    const KConst<Real> K0 = flight_consts<Real>(P0), K1 = flight_consts<Real>(P1);
+    const double f = double(P0.n_slots) / double(P0.n_slots + P1.n_slots);
+    int g = grid < 2 ? 2 : grid;
+    int n0 = (int)(f * g + 0.5);
+    n0 = n0 < 1 ? 1 : (n0 > g - 1 ? g - 1 : n0);
+    if (nw0 && nw1)
+        k_flight_pair<Real, true, true><<<g, block, smem, st>>>(P0, K0, n_steps0, count0, P1, K1, n_steps1, count1, n0);
+    else if (nw0)
+        k_flight_pair<Real, true, false><<<g, block, smem, st>>>(P0, K0, n_steps0, count0, P1, K1, n_steps1, count1, n0);
+    else if (nw1)
+        k_flight_pair<Real, false, true><<<g, block, smem, st>>>(P0, K0, n_steps0, count0, P1, K1, n_steps1, count1, n0);
+    else
+        k_flight_pair<Real, false, false><<<g, block, smem, st>>>(P0, K0, n_steps0, count0, P1, K1, n_steps1, count1, n0);
 }
 template <typename Real>
 void launch_sort(const DevParams& P, const DevParams& alt, bool nw, uint32_t* key, unsigned int* hist,

@@ -400,6 +400,18 @@ class Context:
 OBS_DTYPE = np.dtype(EmcObs)
 
 
+def group_step(ctxs, n_steps: int):
+    """Advance one or two contexts (same stream, precision, block size) by
+    n_steps together: one flight launch per chunk over both (emc_group_step)."""
+    L = lib()
+    if not getattr(L, "_group_ready", False):
+        L.emc_group_step.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32]
+        L.emc_group_step.restype = C.c_int
+        L._group_ready = True
+    hs = (C.c_void_p * len(ctxs))(*[c.h.value if hasattr(c.h, "value") else c.h for c in ctxs])
+    ctxs[0]._check(L.emc_group_step(hs, len(ctxs), int(n_steps)))
+
+
 def obs_dict(o: EmcObs) -> dict:
     return {
         "sum_v": np.array(o.sum_v[:]), "sum_E": o.sum_E, "sum_Etot": o.sum_Etot,

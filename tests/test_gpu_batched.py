@@ -93,3 +93,66 @@ def test_full_mixed_batch_bookkeeping(emc):
     finally:
         for _, ctx in ctxs.values():
             ctx.close()
+
+
+def _batch_for_group():
+    cfgs = W.config_batched(n_ens=12, seed=5, scale=0.01)
+    for i, c in enumerate(cfgs):
+        if c["geometry"] == 1:
+            cfgs[i] = W.nanowire(n_particles=c["n_particles"], Vd=c["Vd"] * 0.2, T=c["T"], Nd_cm3=c["Nd"] * 1e-6,
+                                 seed=c["seed"], nx=20, Lx=200e-9)
+    g = W.by_geometry(cfgs)
+    return [cfgs[i] for i in g[0]], [cfgs[i] for i in g[1]]
+
+
+def _state(emc, ctx):
+    d = ctx.debug_particles()
+    keep = d["valley"] >= 0
+    order = np.lexsort((d["id"][keep], d["ens"][keep]))
+    return {k: v[keep][order] for k, v in d.items()}, {
+        "events": ctx.emc_tally(emc.TALLY_EVENTS_CELL), "cross": ctx.emc_tally(emc.TALLY_CROSSINGS),
+        "charge": ctx.emc_tally(emc.TALLY_CHARGE),
+        "alive": [o["n_alive"] for o in ctx.emc_tally(emc.TALLY_OBS)],
+        "samples": [o["n_samples"] for o in ctx.emc_tally(emc.TALLY_OBS)]}
+
+
+@pytest.mark.parametrize("prec_name,kinds", [("FP64", "bulk+wire"), ("FP32", "bulk+wire"), ("FP32", "wire+wire")])
+def test_group_step_equals_separate_steps(emc, prec_name, kinds):
+    """emc_group_step: the bulk and the nanowire contexts of the mixed batch
+    (or two nanowire contexts) in one flight launch per chunk give the same
+    particles and integer tallies as each context stepped alone, across
+    Poisson periods and a partial one."""
+    prec = getattr(emc, prec_name)
+    bulk, wire = _batch_for_group()
+    pair = (bulk, wire) if kinds == "bulk+wire" else (wire, [dict(c, seed=c["seed"] + 1000) for c in wire])
+    steps = 3 * wire[0]["steps_per_poisson"] + 4
+    alone = []
+    for cf in pair:
+        with emc.Context(cf, precision=prec) as ctx:
+            ctx.emc_step(steps)
+            alone.append(_state(emc, ctx))
+    a, b = emc.Context(pair[0], precision=prec), emc.Context(pair[1], precision=prec)
+    try:
+        emc.emc.group_step([a, b], steps - 4)
+        emc.emc.group_step([a, b], 4)
+        together = [_state(emc, a), _state(emc, b)]
+    finally:
+        a.close()
+        b.close()
+    for (pa, ta), (pb, tb) in zip(alone, together):
+        for k in ("k", "r", "tr", "valley", "ens", "id", "ctr"):
+            assert np.array_equal(pa[k], pb[k]), k
+        for k in ("events", "cross", "charge"):
+            assert np.array_equal(ta[k], tb[k]), k
+        assert ta["alive"] == tb["alive"] and ta["samples"] == tb["samples"]
+
+
+def test_group_step_refuses_mismatched_contexts(emc):
+    bulk, wire = _batch_for_group()
+    with emc.Context(wire) as a, emc.Context([dict(c, seed=c["seed"] + 7) for c in wire]) as b:
+        a.emc_step(3)  # out of phase
+        with pytest.raises(emc.EmcError):
+            emc.emc.group_step([a, b], 10)
+    with emc.Context(bulk) as a, emc.Context(wire, precision=emc.FP64) as b:
+        with pytest.raises(emc.EmcError):
+            emc.emc.group_step([a, b], 10)

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libemc.so")
 UNITS = ["emc.cu", "inst_f32.cu", "inst_f64.cu", "mlp.cu", "thermal.cu"]
-HEADERS = ["common.cuh", "kernels.cuh"]
+HEADERS = ["common.cuh", "kernels.cuh", "phonon.cuh", "trace.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # the float (production) kernels use approximate division and square root;

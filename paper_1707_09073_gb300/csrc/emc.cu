@@ -16,6 +16,7 @@
 
 #include "../../include/emc.h"
 #include "common.cuh"
+#include "trace.h"
 
 namespace emc {
 template <typename Real> void launch_flight(const DevParams&, bool, int, int, int, int, cudaStream_t);
@@ -1340,6 +1341,7 @@ extern "C" {
 
 emc_status emc_batch_init(const emc_config* cfgs, int32_t n_ens, void* stream, emc_ctx** out)
 {
+    EMC_TRACE("emc_batch_init");
     if (!out) return EMC_EINVAL;
     *out = nullptr;
     emc_ctx* ctx = new (std::nothrow) emc_ctx();
@@ -1472,6 +1474,7 @@ emc_status emc_init(const emc_config* cfg, void* stream, emc_ctx** out)
 
 emc_status emc_step(emc_ctx* ctx, int32_t n_steps)
 {
+    EMC_TRACE("emc_step");
     if (!ctx) return EMC_EINVAL;
     if (n_steps < 0) return fail(ctx, EMC_EINVAL, "n_steps < 0");
     if (n_steps == 0) return EMC_OK;
@@ -1482,6 +1485,7 @@ emc_status emc_step(emc_ctx* ctx, int32_t n_steps)
 
 emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_t dst_is_device, int32_t reset)
 {
+    EMC_TRACE("emc_tally");
     if (!ctx || !dst) return EMC_EINVAL;
     const size_t need = tally_bytes(ctx->n_ens, ctx->ncell, kind);
     if (need == 0) return fail(ctx, EMC_EINVAL, "unknown tally kind");
@@ -1495,6 +1499,7 @@ emc_status emc_tally(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_
 
 emc_status emc_tally_async(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, int32_t dst_is_device, int32_t reset)
 {
+    EMC_TRACE("emc_tally_async");
     if (!ctx || !dst) return EMC_EINVAL;
     const int E = ctx->n_ens, C = ctx->ncell;
     const bool nw = ctx->geom == EMC_GEOM_NANOWIRE;
@@ -1544,6 +1549,7 @@ emc_status emc_tally_async(emc_ctx* ctx, int32_t kind, void* dst, size_t bytes, 
 
 emc_status poisson_solve(emc_ctx* ctx, const double* charge_or_null, const double* bc_volts, double* phi_out)
 {
+    EMC_TRACE("poisson_solve");
     if (!ctx || !bc_volts) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "poisson_solve needs the nanowire geometry");
     if (!finite_inputs(charge_or_null, ctx->ncell, bc_volts))
@@ -1663,6 +1669,7 @@ extern "C" {
 emc_status emc_poisson_solve_static(emc_ctx* ctx, const double* charge_or_null, const double* bc_volts,
                                     double* phi_out_or_null)
 {
+    EMC_TRACE("emc_poisson_solve_static");
     if (!ctx || !bc_volts) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE)
         return fail(ctx, EMC_ESTATE, "emc_poisson_solve_static needs the nanowire geometry");
@@ -1786,6 +1793,7 @@ emc_status emc_state_size(emc_ctx* ctx, size_t* bytes)
 
 emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes)
 {
+    EMC_TRACE("emc_get_state");
     if (!ctx || !dst) return EMC_EINVAL;
     if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     const bool tmode = ctx->cell_bin != nullptr;
@@ -1817,6 +1825,7 @@ emc_status emc_get_state(emc_ctx* ctx, void* dst, size_t bytes)
 
 emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes)
 {
+    EMC_TRACE("emc_set_state");
     if (!ctx || !src) return EMC_EINVAL;
     if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     if (bytes < sizeof(StateHeader)) return fail(ctx, EMC_EINVAL, "emc_set_state: blob too small");
@@ -1859,6 +1868,7 @@ emc_status emc_set_state(emc_ctx* ctx, const void* src, size_t bytes)
 
 emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double Vg)
 {
+    EMC_TRACE("emc_set_bias");
     if (!ctx || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
     if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     if (!std::isfinite(Vs) || !std::isfinite(Vd) || !std::isfinite(Vg))
@@ -1880,6 +1890,7 @@ emc_status emc_set_bias(emc_ctx* ctx, int32_t ens, double Vs, double Vd, double 
 
 emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias)
 {
+    EMC_TRACE("emc_set_bias_all");
     if (!ctx || !bias) return EMC_EINVAL;
     if (ctx->shard_pending) return fail(ctx, EMC_EINVAL, "shards: exchange pending (emc_shard_tail)");
     if (ctx->geom != EMC_GEOM_NANOWIRE) return fail(ctx, EMC_ESTATE, "emc_set_bias_all needs the nanowire geometry");
@@ -1896,6 +1907,7 @@ emc_status emc_set_bias_all(emc_ctx* ctx, const double* bias)
 emc_status emc_surrogate_train(emc_ctx* ctx, const emc_mlp_config* net, const float* X, const float* Y, int64_t n,
                                const emc_train_config* tc, float* loss_history)
 {
+    EMC_TRACE("emc_surrogate_train");
     if (!ctx || !net || !X || !Y || !tc) return EMC_EINVAL;
     if (ctx->sur) {
         emc_mlp_destroy(ctx->sur);
@@ -1915,6 +1927,7 @@ emc_status emc_surrogate_train(emc_ctx* ctx, const emc_mlp_config* net, const fl
 
 emc_status emc_surrogate_infer(emc_ctx* ctx, const float* X, float* Y, int64_t n)
 {
+    EMC_TRACE("emc_surrogate_infer");
     if (!ctx || n < 0 || (n > 0 && (!X || !Y))) return EMC_EINVAL;
     if (!ctx->sur) return fail(ctx, EMC_ESTATE, "emc_surrogate_infer: no surrogate trained on this context");
     const emc_status s = emc_mlp_infer(ctx->sur, X, Y, n);
@@ -1954,6 +1967,7 @@ emc_status emc_profile_read(emc_ctx* ctx, double* flight_ms, int64_t* flight_lau
 
 emc_status emc_group_step(emc_ctx* const* ctxs, int32_t n_ctx, int32_t n_steps)
 {
+    EMC_TRACE("emc_group_step");
     if (!ctxs || n_ctx < 1 || n_ctx > 2) return EMC_EINVAL;
     for (int i = 0; i < n_ctx; ++i)
         if (!ctxs[i]) return EMC_EINVAL;
@@ -1974,6 +1988,7 @@ emc_status emc_group_step(emc_ctx* const* ctxs, int32_t n_ctx, int32_t n_steps)
 
 emc_status emc_shard_counts(emc_ctx* ctx, int32_t* charge_out, int64_t* free_out)
 {
+    EMC_TRACE("emc_shard_counts");
     if (!ctx || !charge_out || !free_out) return EMC_EINVAL;
     if (!ctx->sharded || !ctx->shard_pending)
         return fail(ctx, EMC_EINVAL, "emc_shard_counts: no exchange pending (or not a sharded context)");
@@ -1990,6 +2005,7 @@ emc_status emc_shard_counts(emc_ctx* ctx, int32_t* charge_out, int64_t* free_out
 emc_status emc_shard_tail(emc_ctx* ctx, const int32_t* charge_global, const int64_t* free_prefix,
                           const int64_t* free_total, int32_t lead)
 {
+    EMC_TRACE("emc_shard_tail");
     if (!ctx || !charge_global || !free_prefix || !free_total) return EMC_EINVAL;
     if (!ctx->sharded || !ctx->shard_pending)
         return fail(ctx, EMC_EINVAL, "emc_shard_tail: no exchange pending (or not a sharded context)");
@@ -2019,6 +2035,7 @@ emc_status emc_shard_tail(emc_ctx* ctx, const int32_t* charge_global, const int6
 
 emc_status emc_set_temperature(emc_ctx* ctx, int32_t ens, const double* T_cells, int32_t n)
 {
+    EMC_TRACE("emc_set_temperature");
     if (!ctx || !T_cells || ens < 0 || ens >= ctx->n_ens) return EMC_EINVAL;
     if (ctx->geom != EMC_GEOM_NANOWIRE || ctx->n_tab != 1)
         return fail(ctx, EMC_ESTATE, "emc_set_temperature needs a nanowire context whose ensembles share one material/doping");

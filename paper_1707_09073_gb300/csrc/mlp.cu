@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/emc.h"
+#include "trace.h"
 #include "common.cuh"
 
 namespace {
@@ -678,6 +679,7 @@ emc_status emc_mlp_debug_set_error(emc_mlp* m)
 
 emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n)
 {
+    EMC_TRACE("emc_mlp_infer");
     if (!m || (n > 0 && (!X || !Y)) || n < 0) return EMC_EINVAL;
     if (n == 0) return EMC_OK;
     const int64_t chunk = 1 << 16;
@@ -699,6 +701,7 @@ emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n)
 
 emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, float* grad, float* loss)
 {
+    EMC_TRACE("emc_mlp_grad");
     if (!m || !X || !Y || n <= 0) return EMC_EINVAL;
     emc_status s = ensure_batch(m, n);
     if (s != EMC_OK) return s;
@@ -723,6 +726,7 @@ emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, f
 emc_status emc_mlp_train(emc_mlp* m, const float* X, const float* Y, int64_t n, const emc_train_config* tc,
                          float* loss_history)
 {
+    EMC_TRACE("emc_mlp_train");
     if (!m || !X || !Y || n <= 0 || !tc || tc->steps < 0 || tc->batch <= 0) return EMC_EINVAL;
     emc_status s = ensure_batch(m, tc->batch);
     if (s != EMC_OK) return s;

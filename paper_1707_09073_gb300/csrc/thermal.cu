@@ -22,6 +22,7 @@
 #include "../../include/emc.h"
 #include "common.cuh"
 #include "phonon.cuh"
+#include "trace.h"
 
 namespace emc {
 // accessors of the context (defined in emc.cu)
@@ -566,6 +567,7 @@ emc_status emc_interface_conductance(const emc_thermal_config* tc, const double*
 
 emc_status emc_thermal_solve(emc_ctx* ctx, const emc_thermal_config* tc, const double* q, double* T, int32_t* iters)
 {
+    EMC_TRACE("emc_thermal_solve");
     if (!ctx || !tc || !q || !T) return EMC_EINVAL;
     int nx, ny, nz, ne;
     double Lx, Ly, Lz;
@@ -625,6 +627,7 @@ emc_status emc_phonon_solve(emc_ctx* ctx, const emc_thermal_config* tc, const em
                             double* dT, double* t_res_ps, uint64_t* scatterings, uint64_t* emitted,
                             emc_phonon_tally* tally)
 {
+    EMC_TRACE("emc_phonon_solve");
     if (!ctx || !tc || !pc || !q) return EMC_EINVAL;
     int nx, ny, nz, ne;
     double Lx, Ly, Lz;

@@ -33,16 +33,26 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile libemc.so.  checked=True builds the checked variant (array
+    indices and positions verified in the kernels, a violation reported
+    through the device error word) into _build_checked/ instead; load it by
+    setting EMC_LIBRARY to the returned path before the first library call."""
+    bdir = BUILD_CHECKED if checked else BUILD
+    lib_path = os.path.join(bdir, "libemc.so")
+    extra = ["-DEMC_CHECKED"] if checked else []
+    os.makedirs(bdir, exist_ok=True)
     deps_common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "emc.h")]
     nvcc = _nvcc()
 
     def one(unit: str) -> str:
         src = os.path.join(CSRC, unit)
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(bdir, unit.replace(".cu", ".o"))
         if force or _stale(obj, [src] + deps_common):
-            cmd = [nvcc] + ARCH + FLAGS + UNIT_FLAGS.get(unit, []) + ["-c", src, "-o", obj + ".tmp"]
+            cmd = [nvcc] + ARCH + FLAGS + extra + UNIT_FLAGS.get(unit, []) + ["-c", src, "-o", obj + ".tmp"]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {unit}:\n{r.stdout}\n{r.stderr}")
@@ -53,14 +63,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(one, UNITS))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

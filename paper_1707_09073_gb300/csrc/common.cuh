@@ -33,7 +33,21 @@ constexpr double kVk0 = kHbar / kM0 * 1e3;                    // hbar/m0, nm^2/f
 constexpr double kE2Eps0 = kQ / kEps0 * 1e9;                  // e^2/eps0, eV nm (= q/eps0 in V nm)
 
 // error word bits (device -> host)
-enum : int { ERR_FLIGHTS = 1, ERR_NAN = 2, ERR_INIT = 4 };
+enum : int { ERR_FLIGHTS = 1, ERR_NAN = 2, ERR_INIT = 4, ERR_BOUNDS = 8 };
+
+// The checked build (compiled with EMC_CHECKED) verifies array indices and
+// positions in the kernels and sets ERR_BOUNDS in the device error word
+// when one is out of range; the production build compiles the checks away.
+#ifdef EMC_CHECKED
+#define EMC_CHECK(err, cond)                            \
+    do {                                                \
+        if (!(cond)) atomicOr((err), (int)ERR_BOUNDS);  \
+    } while (0)
+#else
+#define EMC_CHECK(err, cond) \
+    do {                     \
+    } while (0)
+#endif
 
 // Final-state physics of one table set, in device units.
 template <typename Real>

@@ -1124,9 +1124,9 @@ emc_status check_err(emc_ctx* ctx)
     CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     if (h) {
-        char buf[128];
+        char buf[192];
         snprintf(buf, sizeof buf, "device error word 0x%x (1: flight loop bound, 2: non-finite particle energy, "
-                                  "4: initial-energy draws)", h);
+                                  "4: initial-energy draws, 8: index out of range (checked build))", h);
         return fail(ctx, EMC_EOVERFLOW, buf);
     }
     return EMC_OK;

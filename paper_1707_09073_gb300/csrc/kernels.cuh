@@ -112,6 +112,7 @@ struct KConst {
     Real Lx, Ly, Lz, inv_dx, inv_dy, inv_dz, p_spec, dt, inv_dE;
     int nx, ny, nz, ncell, nb, nbs, n_tab, n_tab_s;
     int64_t per_block;
+    int* err;  // device error word (checked build)
 };
 
 // Shared-memory tallies of the ensembles [e_base, e_base + WE) of a block.
@@ -181,6 +182,10 @@ __device__ __forceinline__ int cell_of(const KConst<Real>& K, Real x, Real y, Re
     const Real fx = Mth<Real>::floor_(x * K.inv_dx);
     const Real fy = Mth<Real>::floor_(y * K.inv_dy);
     const Real fz = Mth<Real>::floor_(z * K.inv_dz);
+    // a position on a far face belongs to the last subcell; anything further
+    // out is a bug (checked build)
+    EMC_CHECK(K.err, fx > Real(-1) && fx <= Real(K.nx) && fy > Real(-1) && fy <= Real(K.ny) && fz > Real(-1) &&
+                         fz <= Real(K.nz));
     const int ix = fx >= Real(0) ? (fx < Real(K.nx) ? int(fx) : K.nx - 1) : 0;
     const int iy = fy >= Real(0) ? (fy < Real(K.ny) ? int(fy) : K.ny - 1) : 0;
     const int iz = fz >= Real(0) ? (fz < Real(K.nz) ? int(fz) : K.nz - 1) : 0;
@@ -528,6 +533,8 @@ __device__ __forceinline__ void final_state(QEntry<Real>& Q, const DevParams& P,
         // real events per (subcell, valley, mechanism): the subcell heat map
         // (net phonon emission) and the mechanism statistics both follow
         const int c = cell_of<Real>(K, q.x, q.y, q.z);
+        EMC_CHECK(P.err, q.e >= 0 && q.e < P.n_ens && c >= 0 && c < K.ncell && v >= 0 && v < NV && mech >= 0 &&
+                             mech < NM);
         agg_inc_u64(P.events, ((unsigned long long)q.e * K.ncell + c) * (NV * NM) + v * NM + mech);
     } else {
         const int w = q.e - e_base;
@@ -1049,7 +1056,9 @@ __global__ void __launch_bounds__(256) k_inject(const DevParams P)
             const int t = lo;
             const int side = t / nface, rem = t - side * nface;
             const int ix = side ? P.nx - 1 : 0, iy = rem / P.nz, iz = rem - iy * P.nz;
+            EMC_CHECK(P.err, (int64_t)id < P.ens_cap[e] && t >= 0 && t < ncon);
             const int64_t slot = P.slot_of_id[P.ens_off[e] + id];
+            EMC_CHECK(P.err, slot >= P.ens_off[e] && slot < P.ens_off[e] + P.ens_cap[e]);
             Part<Real> q;
             q.e = e;
             q.id = gid_of(P, e, id);
@@ -1184,6 +1193,7 @@ __global__ void k_sort_scatter(const DevParams P, const uint32_t* key, const uns
     if (lane == leader) base = atomicAdd(&cursor[kk], (unsigned)__popc(peers));
     base = __shfl_sync(peers, base, leader);
     const int64_t d = (int64_t)offs[kk] + base + __popc(peers & ((1u << lane) - 1u));
+    EMC_CHECK(P.err, d >= 0 && d < P.n_slots);
     static_cast<Real*>(Q.kx)[d] = static_cast<const Real*>(P.kx)[p];
     static_cast<Real*>(Q.ky)[d] = static_cast<const Real*>(P.ky)[p];
     static_cast<Real*>(Q.kz)[d] = static_cast<const Real*>(P.kz)[p];
@@ -1279,6 +1289,7 @@ KConst<Real> flight_consts(const DevParams& P)
     K.n_tab = P.n_tab;
     K.n_tab_s = P.n_tab <= 64 ? P.n_tab : 0;
     K.per_block = 0;
+    K.err = P.err;
     return K;
 }
 
@@ -1346,6 +1357,7 @@ void launch_sort(const DevParams& P, const DevParams& alt, bool nw, uint32_t* ke
     K.ny = P.ny;
     K.nz = P.nz;
     K.ncell = P.ncell;
+    K.err = P.err;
     const unsigned grid = (unsigned)((P.n_slots + 255) / 256);
     if (phase == 0) {
         if (nw) k_sort_keys<Real, true><<<grid, 256, 0, st>>>(P, K, key, hist);

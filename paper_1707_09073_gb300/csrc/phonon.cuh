@@ -64,6 +64,8 @@ struct PhParams {
     unsigned long long* scat;      // [C]
     unsigned long long* emit;      // [C]
     unsigned long long* out;       // [8]: absorbed per face (6), segments, capped
+    int* err;                      // device error word (checked build: ERR_BOUNDS)
+    int nt, pad3_;                 // rate tables
 };
 
 template <typename Real>
@@ -228,6 +230,8 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
             } else {
                 ++seg;
                 ++n_seg;
+                EMC_CHECK(P.err, c >= 0 && c < C && b >= 0 && b < nb && ix[0] >= 0 && ix[0] < nc[0] && ix[1] >= 0 &&
+                                     ix[1] < nc[1] && ix[2] >= 0 && ix[2] < nc[2] && __ldg(P.tix + c) < P.nt);
                 const Real v = __ldg(vg + b);
                 const Real rr = __ldg(rate + (size_t)__ldg(P.tix + c) * nb + b);
                 // time to the faces of the subcell, the earliest axis first

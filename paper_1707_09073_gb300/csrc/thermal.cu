@@ -472,7 +472,7 @@ emc_status phonon_run(emc_ctx* ctx, const emc_phonon_config& pc, const PhTables&
     PCK(cudaMallocAsync(&d_t12, sizeof(Real) * nb, st));
     PCK(cudaMallocAsync(&d_tix, sizeof(int) * C, st));
     PCK(cudaMallocAsync(&d_neg, sizeof(int) * C, st));
-    const size_t nu = 9 + 3 * (size_t)C;
+    const size_t nu = 10 + 3 * (size_t)C;  // next, out[8], error word, tallies
     PCK(cudaMallocAsync(&d_u, sizeof(unsigned long long) * nu, st));
     PCK(cudaMemcpyAsync(d_vg, vg.data(), sizeof(Real) * nb, cudaMemcpyHostToDevice, st));
     PCK(cudaMemcpyAsync(d_rate, rate.data(), sizeof(Real) * nt * nb, cudaMemcpyHostToDevice, st));
@@ -493,7 +493,9 @@ emc_status phonon_run(emc_ctx* ctx, const emc_phonon_config& pc, const PhTables&
     }
     P.seed = pc.seed;
     P.n_bundles = n; P.first = first; P.max_segments = pc.max_segments;
-    P.next = d_u; P.out = d_u + 1; P.t_res = d_u + 9; P.scat = d_u + 9 + C; P.emit = d_u + 9 + 2 * (size_t)C;
+    P.next = d_u; P.out = d_u + 1; P.err = reinterpret_cast<int*>(d_u + 9);
+    P.t_res = d_u + 10; P.scat = d_u + 10 + C; P.emit = d_u + 10 + 2 * (size_t)C;
+    P.nt = nt;
     const int block = pc.block_size ? pc.block_size : 256;
     const size_t smem = ph_smem_bytes<Real>(C);
     PCK(cudaFuncSetAttribute(k_phonon<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -526,9 +528,10 @@ emc_status phonon_run(emc_ctx* ctx, const emc_phonon_config& pc, const PhTables&
     PCK(cudaStreamSynchronize(st));
 #undef PCK
     for (int k = 0; k < 8; ++k) out8[k] = u[1 + k];
-    t_res->assign(u.begin() + 9, u.begin() + 9 + C);
-    scat->assign(u.begin() + 9 + C, u.begin() + 9 + 2 * C);
-    emit->assign(u.begin() + 9 + 2 * C, u.begin() + 9 + 3 * C);
+    t_res->assign(u.begin() + 10, u.begin() + 10 + C);
+    scat->assign(u.begin() + 10 + C, u.begin() + 10 + 2 * C);
+    emit->assign(u.begin() + 10 + 2 * C, u.begin() + 10 + 3 * C);
+    if (u[9] != 0ull) return ctx_fail(ctx, EMC_EOVERFLOW, "phonon Monte Carlo: index out of range (checked build)");
     return EMC_OK;
 }
 

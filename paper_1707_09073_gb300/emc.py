@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libemc.so")
+# EMC_LIBRARY selects another build of the same library (the checked build
+# of build.build(checked=True)); it must be set before the first call
+LIB_PATH = os.environ.get("EMC_LIBRARY") or os.path.join(HERE, "_build", "libemc.so")
 
 NV, NM = 3, 10
 GEOM_BULK, GEOM_NANOWIRE = 0, 1

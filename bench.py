@@ -770,6 +770,9 @@ def run_emc(args, world: int, rank: int, local: int):
 
     cfg = workload_desc(n_part)
     cfg["parallelism"] = "weak: one full sweep per GPU" if world > 1 else "1 GPU"
+    props = torch.cuda.get_device_properties(dev)
+    cfg["device"] = {"name": props.name, "sms": props.multi_processor_count,
+                     "memory_gib": round(props.total_memory / 2**30, 1), "host_cores": len(os.sched_getaffinity(0))}
     cfg["launch"] = dict(tune, source="autotuner" if tuned else ("command line" if tune else "defaults"))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

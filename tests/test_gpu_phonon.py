@@ -227,3 +227,35 @@ def test_full_size_wire_sampled_bundles_and_bookkeeping(emc):
     np.testing.assert_allclose(s["dT"].reshape(cfg["nx"], -1).mean(axis=1),
                                r["dT"].reshape(cfg["nx"], -1).mean(axis=1), rtol=1e-2,
                                atol=1e-2 * np.abs(r["dT"]).max())
+
+
+def test_electron_to_phonon_chain_matches_oracle(emc, oracle_mod):
+    """One step of the hybrid method through the library (FP64 electron Monte
+    Carlo -> net phonon energy per subcell -> FP64 phonon Monte Carlo ->
+    temperature rise) against the same chain through the oracle (its
+    per-cell events -> net phonon energy -> oracle/phonon.solve): the heat
+    maps are equal, the bundles the same, the temperature rise equal to the
+    fixed-point rounding of the residence times."""
+    from emc_harness import oracle_heat
+    from paper_1707_09073_gb300 import electrothermal as ET
+    cfg = W.nanowire(n_particles=6000, nx=20, Lx=200e-9, Vd=4.0, seed=7)
+    steps = 60
+    ref = oracle_mod.Sim(cfg)
+    ref.run(steps)
+    rt = ref.tallies()
+    Vc = cfg["Lx"] * cfg["Ly"] * cfg["Lz"] / (cfg["nx"] * cfg["ny"] * cfg["nz"])
+    window = steps * cfg["dt"]
+    tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC)
+    pc = emc.emc.phonon_config(emc.emc.WIRE_FACES, n_bins=400, precision=emc.FP64, p_specular=0.3, seed=13)
+    with emc.Context(cfg, precision=emc.FP64) as ctx:
+        ctx.emc_step(steps)
+        q_lib = ET.heat_map(ctx, window)[0]
+        g = emc.emc.phonon_solve(ctx, tc, pc, q_lib, 20_000)
+    w = cfg["Nd"] * cfg["Lx"] * cfg["Ly"] * cfg["Lz"] / cfg["n_particles"]
+    h = oracle_heat(rt["events"])
+    q_orc = (h[:, 0] * cfg["hw_lo_eV"] + h[:, 1] * cfg["hw_iv_eV"]) * 1.602176634e-19 * w / (window * Vc)
+    np.testing.assert_allclose(q_lib, q_orc, rtol=1e-12, atol=1e-12 * np.abs(q_orc).max())
+    r = PH.solve(cfg, q_orc, GAN, emc.emc.WIRE_FACES, 20_000, seed=13, nb=400, p_specular=[0.3] * 6,
+                 substrate=SIC, threads=8)
+    _assert_same_bundles(g, r)
+    assert g["dT"].max() > 0

@@ -369,11 +369,26 @@ def electrothermal_comparison(args, stream) -> dict:
                  "saving_per_run_seconds": saving,
                  "break_even_runs": (t_data + t_train) / saving if saving > 0 else None,
                  "note": "the surrogate is trained once per material and doping range and reused by every sweep"},
+        "cost_to_2pct": _cost_to(out, "mc_runs_to_within_2pct_of_judged_peak", t_data + t_train),
         "surrogate": {"samples": args.sur_samples, "train_steps": 3000, "batch": 1024,
                       "infer_ms_115200_queries": 1e3 * t_infer,
                       "network": "4-128-128-128-7 SiLU, BF16 tcgen05 tensor cores, FP32 accumulation in TMEM"},
     }
     return res
+
+
+def _cost_to(out, key, t_surrogate):
+    """Seconds to reach a peak-rise accuracy (Monte Carlo runs to it times
+    the loop's mean seconds per run), plain against the surrogate warm start,
+    and the sweeps after which the surrogate's data and training pay off."""
+    def secs(m):
+        n = out[m].get(key)
+        return None if n is None else n * out[m]["seconds"] / max(out[m]["mc_iterations"], 1)
+    sp, sw = secs("plain"), secs("surrogate_warm_start")
+    saved = (sp - sw) if (sp is not None and sw is not None) else None
+    return {"criterion": key, "plain_seconds": sp, "surrogate_warm_start_seconds": sw,
+            "saving_per_sweep_seconds": saved,
+            "break_even_sweeps": t_surrogate / saved if saved and saved > 0 else None}
 
 
 # ------------------------------------------------- many-ensemble mixed batch

@@ -19,13 +19,9 @@ def _wire(nx=20, Lx=200e-9):
 
 
 def _heat(cfg, seed=0):
-    """A heat map shaped like the electrons' (rising towards the drain-side
-    gate edge), positive everywhere."""
-    C = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    rng = np.random.default_rng(seed)
-    x = (np.arange(cfg["nx"]) + 0.5) / cfg["nx"]
-    prof = 1.0 + 8.0 * np.exp(-((x - 0.75) / 0.08) ** 2)
-    return (np.repeat(prof, cfg["ny"] * cfg["nz"]) * rng.uniform(0.5, 1.5, C) * 1e17)
+    """The seeded synthetic heat map of workloads.py (shaped like the
+    electrons', with a stretch of net absorption at the source end)."""
+    return W.heat_map(cfg, seed=seed)
 
 
 def _temps(cfg, seed=1):
@@ -202,9 +198,7 @@ def test_full_size_wire_sampled_bundles_and_bookkeeping(emc):
     and in the segment count by 8e-5."""
     cfg = W.nanowire(n_particles=10, Vd=20.0, seed=1)
     C = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    x = (np.arange(cfg["nx"]) + 0.5) / cfg["nx"]
-    q = np.repeat(1.0 + 8.0 * np.exp(-((x - 0.75) / 0.08) ** 2), cfg["ny"] * cfg["nz"]) * 1e17
-    q[: 5 * cfg["ny"] * cfg["nz"]] *= -0.2
+    q = W.heat_map(cfg, seed=3)
     tc = emc.emc.thermal_config(GAN, L_boundary=0.0, substrate=SIC)
     N = 10_000_000
     with emc.Context(cfg) as ctx:

@@ -181,6 +181,21 @@ def config_batched(n_ens: int = 256, seed: int = 0, scale: float = 1.0) -> list[
     return out
 
 
+def heat_map(cfg: dict, peak_W_m3: float = 9.0e17, seed: int = 0) -> "np.ndarray":
+    """Seeded synthetic heat generation per subcell (W/m^3) of a nanowire
+    configuration, shaped like the electrons' at a high drain bias: a floor
+    of 1/9 of the peak along the wire, a Gaussian bump of width 0.08 L at 0.75
+    L (the drain-side gate edge), subcell-to-subcell scatter of +-50%, and a
+    negative stretch (net phonon absorption) over the first 5% of the wire."""
+    import numpy as _np
+    rng = _np.random.default_rng(seed)
+    x = (_np.arange(cfg["nx"]) + 0.5) / cfg["nx"]
+    prof = (1.0 + 8.0 * _np.exp(-((x - 0.75) / 0.08) ** 2)) / 9.0
+    q = _np.repeat(prof, cfg["ny"] * cfg["nz"]) * rng.uniform(0.5, 1.5, cfg["nx"] * cfg["ny"] * cfg["nz"])
+    q[: max(1, cfg["nx"] // 20) * cfg["ny"] * cfg["nz"]] *= -0.2
+    return q * peak_W_m3
+
+
 def by_geometry(cfgs: list[dict]) -> dict[int, list[int]]:
     """Indices of the configurations of each geometry (one context each)."""
     g: dict[int, list[int]] = {}

@@ -326,6 +326,16 @@ class Context:
         self._check(lib().emc_shard_counts(self.h, q.ctypes.data_as(C.c_void_p), f.ctypes.data_as(C.c_void_p)))
         return q, f
 
+    def emc_shard_counts_ptr(self, charge_ptr: int, free_ptr: int):
+        """emc_shard_counts into caller memory given by address (host or
+        device: int32[E][C] and int64[E][2])."""
+        self._check(lib().emc_shard_counts(self.h, C.c_void_p(int(charge_ptr)), C.c_void_p(int(free_ptr))))
+
+    def emc_shard_tail_ptr(self, charge_ptr: int, prefix_ptr: int, total_ptr: int, lead: bool):
+        """emc_shard_tail from caller memory given by address (host or device)."""
+        self._check(lib().emc_shard_tail(self.h, C.c_void_p(int(charge_ptr)), C.c_void_p(int(prefix_ptr)),
+                                         C.c_void_p(int(total_ptr)), int(bool(lead))))
+
     def emc_shard_tail(self, charge_global, free_prefix, free_total, lead: bool):
         """Refill and Poisson update of a sharded context from the wire's
         count (emc_shard_tail)."""

@@ -164,6 +164,8 @@ class DistWire:
 
     def _exchange(self):
         torch, dist = self._torch, self._dist
+        if self.device.type == "cuda" and isinstance(self.ctx, _emc.Context):
+            return self._exchange_device()
         q, f = self.ctx.emc_shard_counts()
         qt = torch.from_numpy(np.ascontiguousarray(q, dtype=np.int64)).to(self.device)
         dist.all_reduce(qt, group=self.group)
@@ -172,6 +174,26 @@ class DistWire:
         dist.all_gather(fall, ft, group=self.group)
         fs = np.stack([t.cpu().numpy() for t in fall])
         self.ctx.emc_shard_tail(*exchange(qt.cpu().numpy(), fs, self.rank))
+
+    def _exchange_device(self):
+        """The exchange in device memory (NCCL): the library writes the
+        counts straight into device tensors, the collectives run on them, the
+        prefix and total of the free-id counts are summed on the device and
+        the library reads them back from there."""
+        torch, dist = self._torch, self._dist
+        E, Cn = self.ctx.n_ens, self.ctx.n_cell
+        if not hasattr(self, "_dq"):
+            self._dq = torch.empty((E, Cn), dtype=torch.int32, device=self.device)
+            self._df = torch.empty((E, 2), dtype=torch.int64, device=self.device)
+            self._dall = torch.empty((self.world, E, 2), dtype=torch.int64, device=self.device)
+        self.ctx.emc_shard_counts_ptr(self._dq.data_ptr(), self._df.data_ptr())
+        dist.all_reduce(self._dq, group=self.group)
+        dist.all_gather_into_tensor(self._dall, self._df, group=self.group)
+        pre = self._dall[:self.rank].sum(dim=0) if self.rank > 0 else torch.zeros_like(self._df)
+        tot = self._dall.sum(dim=0)
+        pre, tot = pre.contiguous(), tot.contiguous()
+        torch.cuda.current_stream(self.device).synchronize()  # the collectives are done
+        self.ctx.emc_shard_tail_ptr(self._dq.data_ptr(), pre.data_ptr(), tot.data_ptr(), self.rank == 0)
 
     def emc_step(self, n: int):
         n = int(n)

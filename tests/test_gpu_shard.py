@@ -191,3 +191,53 @@ def test_sharded_wire_with_subcell_temperatures_and_resume(emc):
         for c in wire.ctxs:
             res_p.update(_particles_by_gid(emc, c, c.cfgs))
     assert res_p == want_p
+
+
+NCCL_SCRIPT = r'''
+import os, numpy as np, torch, torch.distributed as dist
+import workloads as W
+import paper_1707_09073_gb300 as emc
+from paper_1707_09073_gb300 import shard as SH
+torch.cuda.set_device(0)
+dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % int(os.environ["PORT"]), rank=0, world_size=1)
+cfg = W.nanowire(n_particles=9000, nx=20, Lx=200e-9, Vd=3.0, seed=44)
+steps = 5 * cfg["steps_per_poisson"] + 2
+with emc.Context(cfg, precision=emc.FP64) as ctx:
+    ctx.emc_step(steps)
+    want = [ctx.emc_tally(k) for k in (emc.TALLY_EVENTS_CELL, emc.TALLY_CROSSINGS, emc.TALLY_CHARGE, emc.TALLY_PHI)]
+    wp = ctx.debug_particles()
+wire = SH.DistWire(cfg, precision=emc.FP64)
+assert wire.device.type == "cuda"
+wire.emc_step(steps)
+got = [wire.emc_tally(k) for k in (emc.TALLY_EVENTS_CELL, emc.TALLY_CROSSINGS, emc.TALLY_CHARGE, emc.TALLY_PHI)]
+gp = wire.ctx.debug_particles()
+for a, b in zip(want, got):
+    assert np.array_equal(np.asarray(a), np.asarray(b))
+def live(d):
+    return {int(d["id"][s]): (d["k"][s].tobytes(), d["r"][s].tobytes(), int(d["valley"][s]), int(d["ctr"][s]))
+            for s in range(d["id"].size) if d["valley"][s] >= 0}
+assert live(wp) == live(gp)
+wire.close()
+dist.destroy_process_group()
+print("nccl shard ok")
+'''
+
+
+def test_dist_wire_over_nccl_one_rank(emc):
+    """The torch.distributed driver on the NCCL backend (one rank on this
+    GPU; no kernel waits on another rank): the exchange runs in device
+    memory (the library writes and reads the counts there, the collectives
+    run on device tensors) and the run equals the unsharded context bit for
+    bit (FP64)."""
+    import os
+    import socket
+    import subprocess
+    import sys
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PORT=str(port), NCCL_NVLS_ENABLE="0", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", NCCL_SCRIPT], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "nccl shard ok" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]

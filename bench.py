@@ -573,8 +573,10 @@ def phonon_comparison(args, stream) -> dict:
         cores = O.host_cores()
         n_cpu = max(1000, min(N, args.phonon_cpu_bundles))
         # the same geometry, spectrum and faces with a seeded synthetic heat
-        # map of the same shape (the oracle takes no input from the GPU run)
-        qs = W.heat_map(cfg, peak_W_m3=float(np.abs(q).max()), seed=1)
+        # map of the same shape at its default peak (the oracle takes no
+        # input from the GPU run; the bundle weight does not change the
+        # segments a bundle flies)
+        qs = W.heat_map(cfg, seed=1)
         t0 = time.perf_counter()
         ro = PHO.solve(cfg, qs, W.TABLE_II_GAN, emc.emc.WIRE_FACES, n_cpu, seed=77, nb=1000, n_e=cfg["Nd"],
                        elec=W.ELECTRON_PHONON_GAN, substrate=W.TABLE_II_SIC, threads=cores)

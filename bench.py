@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -51,6 +52,30 @@ LANES_PER_SM = 128
 #     (table scan, final energy and |k'|, angle law, sin/cos, orthonormal
 #     basis and rotation, tallies, flight time).
 OPS_STEP, OPS_SELF, OPS_REAL = 98, 133 + 6, 133 + 70
+# The same kind of model for the phonon Monte Carlo kernel (FP32 build),
+# counted from its source:
+#   per flight segment 38: segment cap 1, the three face times from the
+#     reciprocal velocity components 18, scattering time 4, the earliest 2,
+#     position 6, fixed-point residence and its tally 7;
+#   plus 15 per segment that ends on a subcell face (optical depth 3, the
+#     face and the next subcell 12);
+#   per scattering 111 + a binary search of the bin CDF: Philox 4x32-10 60,
+#     four uniforms 12, tally 2, isotropic direction 13, optical depth 3, the
+#     faces ahead 21;
+#   per bundle 111 + two binary searches (subcell CDF, bin CDF) + 50: the
+#     emission (id 5, Philox 60, uniforms 12, subcell index 24, position 9,
+#     tally 2, sign 1) less the scattering tally, and its first direction;
+#   5 per step of a binary search over n entries (ceil(log2 n) steps);
+#   the rough and interface faces' draws are not counted (no tally counts them).
+OPS_PH_SEG, OPS_PH_FACE, OPS_PH_SCAT, OPS_PH_BUNDLE, OPS_PH_SEARCH = 38, 15, 111, 111 + 50, 5
+
+
+def phonon_ops(segments: int, scatterings: int, bundles: int, n_bins: int, n_cells: int) -> float:
+    """Lane operations of the phonon op model for one solve."""
+    sb = OPS_PH_SEARCH * math.ceil(math.log2(n_bins))
+    sc = OPS_PH_SEARCH * math.ceil(math.log2(n_cells))
+    return (OPS_PH_SEG * segments + OPS_PH_FACE * max(segments - scatterings, 0)
+            + (OPS_PH_SCAT + sb) * scatterings + (OPS_PH_BUNDLE + sb + sc) * bundles)
 
 
 def sweep_configs(rank: int, n_particles: int, **tune) -> list[dict]:
@@ -537,6 +562,10 @@ def phonon_comparison(args, stream) -> dict:
         ctx.close()
     P = r["power_W"]
     net = float(q.sum() * cfg["Lx"] * cfg["Ly"] * cfg["Lz"] / q.size)
+    peaks = load_peaks()
+    peak = N_SM * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ops = phonon_ops(r["segments"], r["n_scatterings"], N, 1000, cfg["nx"] * cfg["ny"] * cfg["nz"])
+    achieved = ops / (r["kernel_ms"] * 1e-3) / 1e12
     peak_mc = float(mc["T"].max() - tc.T_sink)
     peak_f = float(T_f[0].max() - tc.T_sink)
     nyz = cfg["ny"] * cfg["nz"]
@@ -547,6 +576,13 @@ def phonon_comparison(args, stream) -> dict:
         "bundles": N, "kernel_ms": r["kernel_ms"], "bundles_per_s": N / (r["kernel_ms"] * 1e-3),
         "segments_per_bundle": r["segments"] / N, "segments_per_s": r["segments"] / (r["kernel_ms"] * 1e-3),
         "scatterings_per_bundle": r["n_scatterings"] / N, "capped": r["capped"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_phonon<float>",
+                     "basis": "lane operations of the phonon op model (bench.py OPS_PH_*: per segment, face, "
+                              "scattering, bundle and binary-search step) over the kernel's CUDA-event time, "
+                              "against 152 SMs x 128 lanes x %.0f MHz" % peaks.get("sm_max_mhz", 2070.0),
+                     "ops_per_segment": ops / max(r["segments"], 1),
+                     "dram": "tables and tallies stay in L2: ~0.1 MB of DRAM per 10^6 bundles (ncu)"},
         "absorbed_share": (np.asarray(r["absorbed"], float) / N).round(4).tolist(),
         "heat_net_W": net, "heat_abs_W": P,
         "peak_rise_K": {"phonon_mc": peak_mc, "fourier": peak_f, "mc_passes": mc["peak_history"]},

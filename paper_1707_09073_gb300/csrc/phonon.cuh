@@ -104,7 +104,8 @@ struct PhM<double> {
 // division), as the oracle rounds it: a bundle that grazes a subcell face
 // splits its time between the two subcells at a point that a one-ulp
 // difference can move visibly.  The production build lets the compiler fuse
-// products and sums and divides with the hardware approximation.
+// products and sums, divides with the hardware approximation and times the
+// faces with reciprocals kept per direction (ph_faces_ahead).
 template <typename Real>
 struct PhA {
     static __device__ __forceinline__ Real mul(Real a, Real b) { return a * b; }
@@ -179,6 +180,22 @@ __device__ __forceinline__ void ph_lambert(int f, Real u1, Real u2, Real d[3])
 }
 
 
+// Production build: per axis the coordinate of the subcell face ahead and
+// the reciprocal of the velocity component, set whenever the direction, the
+// frequency bin or the subcell changes, so that a flight segment needs no
+// division for the faces (a zero component gives an infinite reciprocal and
+// a time that is never the earliest).
+template <typename Real>
+__device__ __forceinline__ void ph_faces_ahead(Real v, const Real d[3], const int ix[3], const Real h[3], Real inv[3],
+                                               Real bnd[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        inv[a] = __fdividef(Real(1), v * d[a]);
+        bnd[a] = Real(ix[a] + (d[a] > Real(0) ? 1 : 0)) * h[a];
+    }
+}
+
 // Dynamic shared memory: t_res (u64) [C], then scatterings and emissions
 // (u32) [C] each.
 template <typename Real>
@@ -219,6 +236,8 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
     int ev = 3, f = 0;
     PhStream st{P.seed, 0u, 0u};
     Real p[3], d[3], depth = Real(0);
+    Real inv[3] = {Real(0), Real(0), Real(0)}, bnd[3] = {Real(0), Real(0), Real(0)};  // production build
+    constexpr bool kFast = std::is_same<Real, float>::value;
     int ix[3] = {0, 0, 0}, c = 0, b = 0;
     long long seg = 0;
     for (;;) {
@@ -240,8 +259,12 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     Real ta = INF;
-                    if (d[a] > Real(0)) ta = A::div(A::sub(A::mul(Real(ix[a] + 1), h[a]), p[a]), A::mul(v, d[a]));
-                    else if (d[a] < Real(0)) ta = A::div(A::sub(A::mul(Real(ix[a]), h[a]), p[a]), A::mul(v, d[a]));
+                    if constexpr (kFast) {
+                        ta = (bnd[a] - p[a]) * inv[a];  // NaN only for a zero component: never taken
+                    } else {
+                        if (d[a] > Real(0)) ta = A::div(A::sub(A::mul(Real(ix[a] + 1), h[a]), p[a]), A::mul(v, d[a]));
+                        else if (d[a] < Real(0)) ta = A::div(A::sub(A::mul(Real(ix[a]), h[a]), p[a]), A::mul(v, d[a]));
+                    }
                     if (ta < Real(0)) ta = Real(0);
                     if (ta < t_exit) {
                         t_exit = ta;
@@ -268,7 +291,10 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
                             p[a] = A::mul(Real(ix[a] + (up ? 1 : 0)), h[a]);
                             const int nxt = ix[a] + (up ? 1 : -1);
                             inside = nxt >= 0 && nxt < nc[a];
-                            if (inside) ix[a] = nxt;
+                            if (inside) {
+                                ix[a] = nxt;
+                                if constexpr (kFast) bnd[a] = Real(nxt + (up ? 1 : 0)) * h[a];
+                            }
                         }
                     }
                     if (inside) {
@@ -282,7 +308,13 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
                         } else if (kind == PH_SPECULAR) {
 #pragma unroll
                             for (int a = 0; a < 3; ++a)
-                                if (a == ax) d[a] = -d[a];
+                                if (a == ax) {
+                                    d[a] = -d[a];
+                                    if constexpr (kFast) {
+                                        inv[a] = -inv[a];
+                                        bnd[a] = Real(ix[a] + (up ? 0 : 1)) * h[a];
+                                    }
+                                }
                         } else {
                             ev = 2;
                         }
@@ -335,6 +367,7 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
                 b = ph_inverse_cdf<Real>(cdf + (size_t)__ldg(P.tix + c) * nb, nb, u0);
                 ph_isotropic<Real>(u01<Real>(r.b), u01<Real>(r.c), d[0], d[1], d[2]);
                 depth = PhM<Real>::neglog(u01<Real>(r.d));
+                if constexpr (kFast) ph_faces_ahead<Real>(__ldg(vg + b), d, ix, h, inv, bnd);
                 ev = 0;
             } else {
                 const int ax = f >> 1;
@@ -353,6 +386,9 @@ __global__ void __launch_bounds__(256) k_phonon(const PhParams P)
                         if (a == ax) d[a] = -d[a];
                 }
                 if (diffuse) ph_lambert<Real>(f, u01<Real>(r.b), u01<Real>(r.c), d);
+                if constexpr (kFast) {
+                    if (ev == 0) ph_faces_ahead<Real>(__ldg(vg + b), d, ix, h, inv, bnd);
+                }
             }
         }
     }

@@ -44,6 +44,8 @@ struct Mth<float> {
     }
     static __device__ __forceinline__ float cospi_(float x) { return cospif(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+    // floor straight to an integer (one conversion; saturates, NaN -> INT_MIN)
+    static __device__ __forceinline__ int floor_i(float x) { return __float2int_rd(x); }
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
 };
@@ -57,6 +59,7 @@ struct Mth<double> {
     static __device__ __forceinline__ void sincos2pi_u(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
     static __device__ __forceinline__ double cospi_(double x) { return cospi(x); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+    static __device__ __forceinline__ int floor_i(double x) { return __double2int_rd(x); }
     static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
     static __device__ __forceinline__ double copysign_(double a, double b) { return copysign(a, b); }
 };
@@ -179,16 +182,17 @@ __device__ __forceinline__ uint32_t gid_of(const DevParams& P, int e, uint32_t i
 template <typename Real>
 __device__ __forceinline__ int cell_of(const KConst<Real>& K, Real x, Real y, Real z)
 {
-    const Real fx = Mth<Real>::floor_(x * K.inv_dx);
-    const Real fy = Mth<Real>::floor_(y * K.inv_dy);
-    const Real fz = Mth<Real>::floor_(z * K.inv_dz);
+    // floor of the scaled coordinate, converted straight to an integer (a
+    // NaN becomes INT_MIN and lands in subcell 0, an overflow saturates)
+    const int fx = Mth<Real>::floor_i(x * K.inv_dx);
+    const int fy = Mth<Real>::floor_i(y * K.inv_dy);
+    const int fz = Mth<Real>::floor_i(z * K.inv_dz);
     // a position on a far face belongs to the last subcell; anything further
     // out is a bug (checked build)
-    EMC_CHECK(K.err, fx > Real(-1) && fx <= Real(K.nx) && fy > Real(-1) && fy <= Real(K.ny) && fz > Real(-1) &&
-                         fz <= Real(K.nz));
-    const int ix = fx >= Real(0) ? (fx < Real(K.nx) ? int(fx) : K.nx - 1) : 0;
-    const int iy = fy >= Real(0) ? (fy < Real(K.ny) ? int(fy) : K.ny - 1) : 0;
-    const int iz = fz >= Real(0) ? (fz < Real(K.nz) ? int(fz) : K.nz - 1) : 0;
+    EMC_CHECK(K.err, fx >= 0 && fx <= K.nx && fy >= 0 && fy <= K.ny && fz >= 0 && fz <= K.nz);
+    const int ix = min(max(fx, 0), K.nx - 1);
+    const int iy = min(max(fy, 0), K.ny - 1);
+    const int iz = min(max(fz, 0), K.nz - 1);
     return (ix * K.ny + iy) * K.nz + iz;
 }
 
@@ -410,13 +414,13 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
         u0 = u0 * static_cast<const Real*>(P.ens_g0)[(size_t)q.e * NV + v] * pb.inv_g0[v];
         Q.beta2 = pb.beta2;
     }
-    const Real fb = Mth<Real>::floor_(E * K.inv_dE);
+    const int fb = Mth<Real>::floor_i(E * K.inv_dE);  // NaN -> INT_MIN
     int b;
-    if (fb >= Real(K.nb)) {
+    if (fb >= K.nb) {
         b = K.nb - 1;
         tally_cnt(bt, P, q.e, e_base, CNT_OVERFLOW, 1u);
-    } else if (fb >= Real(0)) {
-        b = int(fb);
+    } else if (fb >= 0) {
+        b = fb;
     } else {
         b = 0;
         if (!(E == E)) atomicOr(P.err, ERR_NAN);

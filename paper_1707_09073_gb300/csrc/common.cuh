@@ -14,6 +14,10 @@ constexpr int NM = 10;  // mechanisms per valley (see include/emc.h)
 constexpr int WE = 32;  // ensembles with shared-memory block tallies (by index)
 constexpr uint32_t DEAD = 0xFFu;
 constexpr int MAX_FLIGHTS_PER_STEP = 1 << 16;
+#ifndef EMC_CHUNK_RUN
+#define EMC_CHUNK_RUN 2
+#endif
+constexpr int kChunkRun = EMC_CHUNK_RUN;  // consecutive 32-slot chunks a warp of the flight kernel takes
 // per-subcell lattice temperature: rates tabulated on bins T_k = 250 K + 5 K k
 constexpr double TBIN_LO = 250.0, TBIN_DT = 5.0;
 constexpr int NTBIN = 151;

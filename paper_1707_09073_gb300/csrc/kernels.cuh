@@ -731,7 +731,15 @@ __device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Rea
     const int64_t warps = (int64_t)nblk * (blockDim.x >> 5);
     const int64_t n_chunks = (P.n_slots + 31) >> 5;
     Samples<Real> S;
-    for (int64_t c = (int64_t)blk * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+    // runs of kChunkRun consecutive chunks per warp, the runs dealt round
+    // robin: a lane's next particle is most often of the same ensemble, so
+    // its samples are handed over (a warp-wide reduction) once per run.
+    // Two measured fastest on the sorted 21 x 200,000 sweep (1.76e9 real
+    // events/s against 1.74e9 for one, 1.61e9 for four, 1.50e9 for eight:
+    // longer runs put too much of a sorted stretch on one warp)
+    const int64_t w0 = (int64_t)blk * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int64_t c0 = w0 * kChunkRun; c0 < n_chunks; c0 += warps * kChunkRun)
+    for (int64_t c = c0; c < c0 + kChunkRun && c < n_chunks; ++c) {
         const int64_t p = c * 32 + lane;
         const uint32_t tg = (p < P.n_slots) ? P.tag[p] : uint32_t(DEAD);
         const bool valid = (tg & 0xFFu) != DEAD;

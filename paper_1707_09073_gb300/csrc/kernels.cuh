@@ -78,6 +78,16 @@ __device__ __forceinline__ Real kane_E(Real g, Real a)
     return Real(2) * g / (Real(1) + Mth<Real>::sqrt_(fma_(Real(4) * a, g, Real(1))));
 }
 
+// The same energy and s = sqrt(1 + 4ag), which equals 1 + 2aE (the group
+// velocity's denominator): the float build takes it from here instead of
+// forming 1 + 2aE again.
+template <typename Real>
+__device__ __forceinline__ Real kane_E_s(Real g, Real a, Real& s)
+{
+    s = Mth<Real>::sqrt_(fma_(Real(4) * a, g, Real(1)));
+    return Real(2) * g / (Real(1) + s);
+}
+
 // |k|^2
 template <typename Real>
 __device__ __forceinline__ Real norm2(Real x, Real y, Real z)
@@ -285,9 +295,11 @@ __device__ __forceinline__ void drift(Part<Real>& q, const Phys<Real>& ph, const
     const int v = q.v;
     const Real al = ph.alpha[v];
     const Real E0 = q.E;
-    const Real E1 = kane_E(ph.ck[v] * norm2(q.kx, q.ky, q.kz), al);
+    Real s1;
+    const Real E1 = kane_E_s(ph.ck[v] * norm2(q.kx, q.ky, q.kz), al, s1);
     q.E = E1;
-    const Real f1 = ph.vk[v] / fma_(Real(2) * al, E1, Real(1));
+    // the parity build forms 1 + 2 alpha E as the oracle does
+    const Real f1 = ph.vk[v] / (std::is_same<Real, float>::value ? s1 : fma_(Real(2) * al, E1, Real(1)));
     if (NW) {
         const Real f0 = q.f;
         const Real h = Real(0.5) * t;
@@ -344,28 +356,32 @@ __device__ __forceinline__ bool walls(Part<Real>& q, const DevParams& P, const K
         tally_cnt(bt, P, q.e, e_base, out, 1u);
         return true;  // the caller frees the id
     }
+    // a reflected coordinate is kept inside the box (a position that was
+    // inside needs no clamp)
     if (q.y < Real(0)) {
         q.y = -q.y;
+        q.y = q.y > K.Ly ? K.Ly : q.y;
         q.ky = -q.ky;
     } else if (q.y > K.Ly) {
         q.y = Real(2) * K.Ly - q.y;
+        q.y = q.y < Real(0) ? Real(0) : q.y;
         const U4 r = q.draw();
         if (u01<Real>(r.a) < K.p_spec) q.ky = -q.ky;
         else diffuse(q, 1, Real(-1), r);
     }
-    q.y = q.y < Real(0) ? Real(0) : (q.y > K.Ly ? K.Ly : q.y);
     if (q.z < Real(0)) {
         q.z = -q.z;
+        q.z = q.z > K.Lz ? K.Lz : q.z;
         const U4 r = q.draw();
         if (u01<Real>(r.a) < K.p_spec) q.kz = -q.kz;
         else diffuse(q, 2, Real(1), r);
     } else if (q.z > K.Lz) {
         q.z = Real(2) * K.Lz - q.z;
+        q.z = q.z < Real(0) ? Real(0) : q.z;
         const U4 r = q.draw();
         if (u01<Real>(r.a) < K.p_spec) q.kz = -q.kz;
         else diffuse(q, 2, Real(-1), r);
     }
-    q.z = q.z < Real(0) ? Real(0) : (q.z > K.Lz ? K.Lz : q.z);
     return false;
 }
 

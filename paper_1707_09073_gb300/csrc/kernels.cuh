@@ -589,7 +589,7 @@ struct Samples {
     unsigned long long nv = 0ull;
     int e = -1;
 
-    __device__ __forceinline__ void count_valley(int vv) { nv += 1ull << (21 * vv); }
+    __device__ __forceinline__ void count_valley(int vv, unsigned int n) { nv += (unsigned long long)n << (21 * vv); }
     __device__ __forceinline__ unsigned int nvalley(int vv) const { return unsigned((nv >> (21 * vv)) & 0x1FFFFFull); }
 
     // Called by all 32 lanes of the warp; lanes with `need` set hand over
@@ -806,6 +806,7 @@ __device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Rea
             }
         }
         StepSums<Real> ss;
+        unsigned int nsv = 0u;  // step ends in the particle's current valley, not yet counted
         // The warp runs in step: each round the lanes without a pending
         // scattering take one free flight (to the end of their step or to
         // their next scattering, through the walls); the pending scatterings
@@ -842,7 +843,7 @@ __device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Rea
                 }
                 if (step_end) {
                     ss.add(S, q.f * q.kx, q.f * q.ky, q.f * q.kz, q.E, q.E + ph.Ec[q.v]);
-                    S.count_valley(q.v);
+                    ++nsv;
                     ++s;
                     it = 0;
                     tleft = dt;
@@ -862,12 +863,18 @@ __device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Rea
             if (work == 0u) break;
             if (3 * __popc(pend) < __popc(work)) continue;
             if (pending) {
-                if (choose<Real>(Q, P, K, ph, tab_s, nbs1, tab_g, bt, e_base) >= 0)
+                if (choose<Real>(Q, P, K, ph, tab_s, nbs1, tab_g, bt, e_base) >= 0) {
+                    if (Q.mech >= 4) {  // intervalley: the step ends so far were in the old valley
+                        S.count_valley(q.v, nsv);
+                        nsv = 0u;
+                    }
                     final_state<Real, NW>(Q, P, K, ph, bt, e_base);
+                }
                 pending = false;
             }
         }
         if (valid) {
+            S.count_valley(q.v, nsv);
             ss.fold(S);
             store<Real>(P, p, q, NW);
             P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);

@@ -645,22 +645,24 @@ struct Samples {
 // to the accumulators directly, in step order.
 template <typename Real>
 struct StepSums {
-    Real v0 = 0, v1 = 0, v2 = 0, E = 0, Et = 0;
-    __device__ __forceinline__ void add(Samples<Real>&, Real a, Real b, Real c, Real d, Real e)
+    // the total energy's valley-edge part is added once per stretch of steps
+    // in one valley (add_ec), not per step
+    Real v0 = 0, v1 = 0, v2 = 0, E = 0, Ec = 0;
+    __device__ __forceinline__ void add(Samples<Real>&, Real a, Real b, Real c, Real d, Real)
     {
         v0 += a;
         v1 += b;
         v2 += c;
         E += d;
-        Et += e;
     }
+    __device__ __forceinline__ void add_ec(Real x) { Ec += x; }
     __device__ __forceinline__ void fold(Samples<Real>& S) const
     {
         S.v[0].add(v0);
         S.v[1].add(v1);
         S.v[2].add(v2);
         S.E.add(E);
-        S.Et.add(Et);
+        S.Et.add(E + Ec);
     }
 };
 template <>
@@ -673,6 +675,7 @@ struct StepSums<double> {
         S.E.add(d);
         S.Et.add(e);
     }
+    __device__ __forceinline__ void add_ec(double) {}  // added per step, in step order
     __device__ __forceinline__ void fold(Samples<double>&) const {}
 };
 
@@ -866,6 +869,7 @@ __device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Rea
                 if (choose<Real>(Q, P, K, ph, tab_s, nbs1, tab_g, bt, e_base) >= 0) {
                     if (Q.mech >= 4) {  // intervalley: the step ends so far were in the old valley
                         S.count_valley(q.v, nsv);
+                        ss.add_ec(Real(nsv) * ph.Ec[q.v]);
                         nsv = 0u;
                     }
                     final_state<Real, NW>(Q, P, K, ph, bt, e_base);
@@ -875,6 +879,7 @@ __device__ __forceinline__ void flight_body(const DevParams& P, const KConst<Rea
         }
         if (valid) {
             S.count_valley(q.v, nsv);
+            ss.add_ec(Real(nsv) * ph.Ec[q.v]);
             ss.fold(S);
             store<Real>(P, p, q, NW);
             P.tag[p] = (uint32_t(q.e) << 8) | (live ? uint32_t(q.v) : DEAD);

@@ -986,7 +986,7 @@ __device__ __forceinline__ void free_split(uint32_t word, int64_t w, int64_t n0,
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) k_inject(const DevParams P)
+__global__ void __launch_bounds__(1024) k_inject(const DevParams P)
 {
     extern __shared__ long long shl[];
     const int e = blockIdx.x;
@@ -1429,7 +1429,10 @@ void launch_init(const DevParams& P, bool nw, cudaStream_t st)
 template <typename Real>
 void launch_inject(const DevParams& P, cudaStream_t st)
 {
-    const int block = 256;
+    // one block per ensemble (the bitmap is ranked and cleared by one block):
+    // the widest block shortens each thread's stretch of the bitmap
+    // (measured: 1024 threads 0.9% faster per Poisson period than 256)
+    const int block = 1024;
     const size_t smem = sizeof(long long) * block + sizeof(int) * (2 * P.ny * P.nz + 1 + INJ);
     k_inject<Real><<<P.n_ens, block, smem, st>>>(P);
 }

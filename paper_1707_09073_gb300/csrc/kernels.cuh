@@ -44,7 +44,7 @@ struct Mth<float> {
     }
     static __device__ __forceinline__ float cospi_(float x) { return cospif(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
-    // floor straight to an integer (one conversion; saturates, NaN -> INT_MIN)
+    // floor straight to an integer (one conversion; saturates, NaN -> 0)
     static __device__ __forceinline__ int floor_i(float x) { return __float2int_rd(x); }
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float copysign_(float a, float b) { return copysignf(a, b); }
@@ -193,13 +193,14 @@ template <typename Real>
 __device__ __forceinline__ int cell_of(const KConst<Real>& K, Real x, Real y, Real z)
 {
     // floor of the scaled coordinate, converted straight to an integer (a
-    // NaN becomes INT_MIN and lands in subcell 0, an overflow saturates)
+    // NaN converts to 0 and lands in subcell 0, an overflow saturates)
     const int fx = Mth<Real>::floor_i(x * K.inv_dx);
     const int fy = Mth<Real>::floor_i(y * K.inv_dy);
     const int fz = Mth<Real>::floor_i(z * K.inv_dz);
     // a position on a far face belongs to the last subcell; anything further
-    // out is a bug (checked build)
-    EMC_CHECK(K.err, fx >= 0 && fx <= K.nx && fy >= 0 && fy <= K.ny && fz >= 0 && fz <= K.nz);
+    // out, or not a number, is a bug (checked build)
+    EMC_CHECK(K.err, fx >= 0 && fx <= K.nx && fy >= 0 && fy <= K.ny && fz >= 0 && fz <= K.nz && x == x && y == y &&
+                         z == z);
     const int ix = min(max(fx, 0), K.nx - 1);
     const int iy = min(max(fy, 0), K.ny - 1);
     const int iz = min(max(fz, 0), K.nz - 1);
@@ -430,17 +431,15 @@ __device__ __forceinline__ int choose(QEntry<Real>& Q, const DevParams& P, const
         u0 = u0 * static_cast<const Real*>(P.ens_g0)[(size_t)q.e * NV + v] * pb.inv_g0[v];
         Q.beta2 = pb.beta2;
     }
-    const int fb = Mth<Real>::floor_i(E * K.inv_dE);  // NaN -> INT_MIN
+    const int fb = Mth<Real>::floor_i(E * K.inv_dE);  // a NaN converts to 0: caught below
     int b;
     if (fb >= K.nb) {
         b = K.nb - 1;
         tally_cnt(bt, P, q.e, e_base, CNT_OVERFLOW, 1u);
-    } else if (fb >= 0) {
-        b = fb;
     } else {
-        b = 0;
-        if (!(E == E)) atomicOr(P.err, ERR_NAN);
+        b = fb >= 0 ? fb : 0;
     }
+    if (!(E == E)) atomicOr(P.err, ERR_NAN);
     const Real* row = (bn >= 0) ? static_cast<const Real*>(P.bin_table) + (((size_t)bn * NV + v) * K.nb + b) * NM
                     : (b < nbs) ? tab_s + ((size_t)v * nbs + b) * NM : tab_g + ((size_t)v * K.nb + b) * NM;
     int mech = -1;

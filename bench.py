@@ -276,9 +276,9 @@ def electrothermal_comparison(args, stream) -> dict:
     heat map (heat per electron at each subcell's field x the subcell's
     electron density -> Fourier).  Every loop stops
     when no subcell temperature changes by more than max(0.1 K, the Monte
-    Carlo noise of the iteration), and every result is then judged by one
+    Carlo noise of the iteration), and every result is then refereed by one
     long plain Monte Carlo window + Fourier solve at the temperatures the
-    loop returned; the peak rises compared are the judge's."""
+    loop returned; the peak rises compared are the referee's."""
     import numpy as np
     import paper_1707_09073_gb300 as emc
     from paper_1707_09073_gb300 import electrothermal as ET
@@ -328,32 +328,32 @@ def electrothermal_comparison(args, stream) -> dict:
                 T0 = ET.surrogate_heat_start(ctx, sur, tc)
                 r = ET.iterate(ctx, tc, T0, max_iter=15, stop_K=0.1)
             secs = time.perf_counter() - t0
-            j = ET.judge(ctx, tc, r["T"], avg_steps=args.et_judge_steps)
+            j = ET.referee(ctx, tc, r["T"], avg_steps=args.et_referee_steps)
             out[mode] = {"converged": r["converged"], "mc_iterations": r["iterations"], "seconds": secs,
                          "surrogate_seconds": r.get("surrogate_seconds", 0.0),
                          "peak_rise_K_max_bias_history": [round(float(h[-1]), 2) for h in r["history"]],
                          "max_dT_K_history": [round(x, 3) for x in r["max_dT_K"]],
                          "noise_K_history": [round(x, 3) for x in r["noise_K"]],
-                         "judge_peak_rise_K_max_bias": float(j["peak"][-1]),
-                         "judge_peak_se_K_max_bias": float(j["peak_se"][-1]),
-                         "judge_max_dT_K": float(j["max_dT_K"].max()),
+                         "referee_peak_rise_K_max_bias": float(j["peak"][-1]),
+                         "referee_peak_se_K_max_bias": float(j["peak_se"][-1]),
+                         "referee_max_dT_K": float(j["max_dT_K"].max()),
                          "steady_start": {"steady": ss["steady"], "windows_of_200_steps": ss["windows"]},
-                         "_judge": j, "_r": r}
+                         "_referee": j, "_r": r}
         finally:
             ctx.close()
-    plain = out["plain"]["_judge"]
+    plain = out["plain"]["_referee"]
     hot = plain["peak"] >= 5.0
     # accuracy per Monte Carlo run: the first iteration whose peak rise at the
-    # highest bias is within 2% / 1% of the judged plain fixed point
+    # highest bias is within 2% / 1% of the refereed plain fixed point
     ref_pk = float(plain["peak"][-1])
     for m in out:
         h = [float(x[-1]) for x in out[m]["_r"]["history"]]
         for tol in (0.02, 0.01):
             it = next((i + 1 for i, x in enumerate(h) if abs(x - ref_pk) <= tol * ref_pk), None)
-            out[m]["mc_runs_to_within_%dpct_of_judged_peak" % round(100 * tol)] = it
+            out[m]["mc_runs_to_within_%dpct_of_refereed_peak" % round(100 * tol)] = it
     cmp = {}
     for mode in ("surrogate_warm_start", "surrogate", "surrogate_heat_start"):
-        jm = out[mode]["_judge"]
+        jm = out[mode]["_referee"]
         d = jm["peak"] - plain["peak"]
         se = np.hypot(jm["peak_se"], plain["peak_se"])
         rel = np.abs(d[hot]) / plain["peak"][hot]
@@ -377,16 +377,16 @@ def electrothermal_comparison(args, stream) -> dict:
                     "dispersions, R_K(300 K) = %.3g m2K/W) over %g times the wire's footprint%s; "
                     "each loop stops when no subcell temperature changes by more than "
                     "max(0.1 K, the largest difference between the temperatures of the two half-window heat maps); "
-                    "every result judged by a %d-step plain Monte Carlo window + Fourier solve"
+                    "every result refereed by a %d-step plain Monte Carlo window + Fourier solve"
                     % (nb, args.et_particles, 1.0 / float(emc.emc.interface_conductance(tc, [300.0])[0]),
                        args.interface_area_ratio,
                        ("" if args.h_bottom <= 0 else ", lumped %.1e W/m2/K in series" % args.h_bottom),
-                       args.et_judge_steps),
+                       args.et_referee_steps),
         "plain_mc": {k: v for k, v in out["plain"].items() if not k.startswith("_")},
         "surrogate_warm_start": {k: v for k, v in out["surrogate_warm_start"].items() if not k.startswith("_")},
         "surrogate_corrected": {k: v for k, v in out["surrogate"].items() if not k.startswith("_")},
         "surrogate_heat_start": {k: v for k, v in out["surrogate_heat_start"].items() if not k.startswith("_")},
-        "judged_peak_rise_vs_plain": cmp,
+        "refereed_peak_rise_vs_plain": cmp,
         "speedup": out["plain"]["seconds"] / max(out["surrogate_warm_start"]["seconds"], 1e-9),
         "mc_iterations": {m: out[m]["mc_iterations"] for m in out},
         "R_th_vs_Vd": rth,
@@ -394,7 +394,7 @@ def electrothermal_comparison(args, stream) -> dict:
                  "saving_per_run_seconds": saving,
                  "break_even_runs": (t_data + t_train) / saving if saving > 0 else None,
                  "note": "the surrogate is trained once per material and doping range and reused by every sweep"},
-        "cost_to_2pct": _cost_to(out, "mc_runs_to_within_2pct_of_judged_peak", t_data + t_train),
+        "cost_to_2pct": _cost_to(out, "mc_runs_to_within_2pct_of_refereed_peak", t_data + t_train),
         "surrogate": {"samples": args.sur_samples, "train_steps": 3000, "batch": 1024,
                       "infer_ms_115200_queries": 1e3 * t_infer,
                       "network": "4-128-128-128-7 SiLU, BF16 tcgen05 tensor cores, FP32 accumulation in TMEM"},
@@ -882,7 +882,7 @@ def main():
     ap.add_argument("--phonon-loop-bundles", type=int, default=2_000_000)
     ap.add_argument("--et-biases", type=int, default=64)
     ap.add_argument("--et-particles", type=int, default=100_000)
-    ap.add_argument("--et-judge-steps", type=int, default=5000)
+    ap.add_argument("--et-referee-steps", type=int, default=5000)
     ap.add_argument("--sur-samples", type=int, default=100_000)
     ap.add_argument("--h-bottom", type=float, default=0.0,
                     help="lumped conductance under the interface, W/m2/K (0: none)")

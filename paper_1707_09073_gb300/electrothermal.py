@@ -171,10 +171,10 @@ def hybrid_iterate(ctx, tc, pc, T0: np.ndarray, n_bundles: int, warm_steps: int 
     return _result(ctx, tc, T, q, max_iter, False, hist, d_hist, n_hist, t0)
 
 
-def judge(ctx, tc, T: np.ndarray, warm_steps: int = 300, avg_steps: int = 5000) -> dict:
-    """The plain Monte Carlo's verdict on a temperature field: one long
+def referee(ctx, tc, T: np.ndarray, warm_steps: int = 300, avg_steps: int = 5000) -> dict:
+    """The plain Monte Carlo's assessment of a temperature field: one long
     Monte Carlo window at the subcell temperatures T, then the Fourier solve
-    of its heat.  Any loop's result is judged this way, so loops are
+    of its heat.  Any loop's result is refereed this way, so loops are
     compared on the temperatures the Monte Carlo itself gives back."""
     q, qa, qb = mc_heat_halves(ctx, T, warm_steps, avg_steps)
     Tj, _ = _emc.thermal_solve(ctx, tc, q, T)

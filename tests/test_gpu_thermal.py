@@ -53,11 +53,11 @@ def test_electrothermal_surrogate_gains(emc):
     surrogate warm start (its first Fourier step corrected by the surrogate
     for the temperatures it leads to, the plain iteration after it) both
     converge (no subcell temperature changes by more than max(0.1 K, the
-    Monte Carlo noise)), and the plain Monte Carlo judge finds the same peak
+    Monte Carlo noise)), and the plain Monte Carlo referee finds the same peak
     rise at both results (within 3% or 3 standard errors).  What the network
     gains is accuracy per Monte Carlo run: the warm start's first iterate is
-    closer to the judged peak than the plain loop's, and it reaches 2%, 1% and
-    0.5% of it (or the judge's noise) in no more Monte Carlo runs, and one of
+    closer to the refereed peak than the plain loop's, and it reaches 2%, 1% and
+    0.5% of it (or the referee's noise) in no more Monte Carlo runs, and one of
     them in fewer.  (Runs to the stop test are reported by the
     bench: near the Monte Carlo noise they are not shortened.)"""
     from paper_1707_09073_gb300 import electrothermal as ET
@@ -76,7 +76,7 @@ def test_electrothermal_surrogate_gains(emc):
             T0 = np.full((2, ctx.n_cell), 300.0)
             r = (ET.iterate(ctx, tc, T0, max_iter=12) if mode == "plain"
                  else ET.surrogate_accelerated(ctx, sur, tc, T0, max_iter=12, corrected_iters=1))
-            res[mode] = (r, ET.judge(ctx, tc, r["T"], avg_steps=3000))
+            res[mode] = (r, ET.referee(ctx, tc, r["T"], avg_steps=3000))
     (rp, jp), (rs, js) = res["plain"], res["warm"]
     assert rp["converged"] and rs["converged"], (rp["history"], rs["history"])
     assert (jp["peak"] > 1.0).all()
@@ -87,7 +87,7 @@ def test_electrothermal_surrogate_gains(emc):
     assert first_s.max() < first_p.max(), (first_s, first_p)
 
     def runs_to(hist, tol):
-        # within tol of the judged peak, or within the judge's noise
+        # within tol of the refereed peak, or within the referee's noise
         lim = np.maximum(tol * jp["peak"], 3 * jp["peak_se"])
         return next((i + 1 for i, h in enumerate(hist) if np.all(np.abs(h - jp["peak"]) <= lim)), len(hist) + 1)
 

@@ -382,8 +382,17 @@ emc_status emc_mlp_create(const emc_mlp_config* cfg, void* cuda_stream, emc_mlp*
  * error of the normalised outputs).  loss_history: host float[steps] or NULL. */
 emc_status emc_mlp_train(emc_mlp* m, const float* X, const float* Y, int64_t n, const emc_train_config* tc,
                          float* loss_history);
-/* Y [n][n_out] = network(X [n][n_in]); host arrays. */
+/* Y [n][n_out] = network(X [n][n_in]); host arrays.  By default the whole
+ * network runs in one fused tensor-core launch per chunk of rows (every
+ * layer's BF16 weights and a 128-row activation tile held in shared memory,
+ * the accumulator in tensor memory) when the weights fit in shared memory
+ * (about 200 KB with the tile), else one GEMM launch per layer. */
 emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n);
+/* Inference path of emc_mlp_infer: enable = 1 (default) fused when the
+ * network fits, 0 one launch per layer.  Both compute the same arithmetic
+ * (normalisation, BF16 operands, FP32 accumulation, bias and SiLU in FP32).
+ * Errors: EMC_EINVAL for a null handle. */
+emc_status emc_mlp_set_fused(emc_mlp* m, int32_t enable);
 /* Loss and gradient of the loss w.r.t. the parameter vector on host rows
  * X, Y (no update).  grad: host float[count] (see emc_mlp_params). */
 emc_status emc_mlp_grad(emc_mlp* m, const float* X, const float* Y, int64_t n, float* grad, float* loss);

@@ -51,6 +51,9 @@ struct emc_mlp {
     int* d_err = nullptr;  // set by a tensor-core wait that expired
     float *Xall = nullptr, *Yall = nullptr;
     int64_t nall = 0;
+    bool fused = true;                     // inference in one fused launch when the network fits
+    float *fX = nullptr, *fY = nullptr;    // its input and output rows
+    int64_t fcap = 0;
     int64_t step = 0;
     std::vector<void*> allocs;
     std::string err;
@@ -345,6 +348,179 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
 
 constexpr size_t kTcMaxSmem = 2 * (kTcStageA + (size_t)256 * kTcBK * 2);
 
+// ------------------------------------------------------------ fused
+// Inference of the whole network in one launch: a persistent CTA of
+// 4 x kFzGroups warps stages every layer's BF16 weights once in shared memory (the
+// canonical K-major layout without swizzle of k_gemm_tc, here over a
+// layer's whole K: 8-row groups K * 16 bytes apart), then walks 128-row
+// tiles of the input.  Per tile and layer: the activations sit in shared
+// memory, one thread issues the K/16 MMAs into the tensor-memory
+// accumulator and commits them to an mbarrier; after the wait warp w reads
+// rows 32 (w % 4) .. + 31 (the tensor-memory lanes its quarter may access)
+// of every kFzGroups-th 16-column chunk, from chunk w / 4 on, back
+// (tcgen05.ld), adds the bias, applies SiLU (hidden layers) and writes the
+// next layer's BF16 activations over the ones the finished MMAs read; the
+// last layer's outputs are de-normalised into Y.
+// Only the inputs are read and the outputs written.  The arithmetic is the
+// layer-by-layer path's (same normalisation, the same MMAs in the same
+// order, bias and SiLU in FP32, BF16 rounding of the activations).
+struct FusedNet {
+    const __nv_bfloat16* W[kMaxLayers];  // [out_p][in_p], BF16
+    const float* b[kMaxLayers];          // [out_p]
+    uint32_t w_off[kMaxLayers];          // byte offset of layer l's weights in shared memory
+    int in_p[kMaxLayers], out_p[kMaxLayers];
+    int n_layers, n_in, n_out;
+    uint32_t a_off;                      // byte offset of the activation tile
+    uint32_t ncols;                      // tensor-memory columns (power of two >= every out_p, >= 32)
+};
+
+__device__ __forceinline__ uint4 pack_bf16x8(const float* v)
+{
+    uint4 pk;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return pk;
+}
+
+constexpr int kFzGroups = 4;  // column groups: 128 x kFzGroups threads per CTA
+
+__global__ void __launch_bounds__(128 * kFzGroups) k_mlp_fused(const FusedNet N, const float* __restrict__ X, int64_t n,
+                                                   const float* __restrict__ norm, float* __restrict__ Y, int* err)
+{
+    extern __shared__ __align__(1024) unsigned char fz_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int rt = tid & 127, grp = tid >> 7;  // row within the tile, column group
+    const uint32_t bar0 = smem_u32(&bar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(N.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    // every layer's weights, 16-byte chunks into the core-matrix layout
+    for (int l = 0; l < N.n_layers; ++l) {
+        const int K = N.in_p[l], nch = K >> 3, total = N.out_p[l] * nch;
+        unsigned char* dst = fz_smem + N.w_off[l];
+        const uint4* src = reinterpret_cast<const uint4*>(N.W[l]);
+        for (int i = tid; i < total; i += blockDim.x) {
+            const int r = i / nch, c = i - r * nch;
+            *reinterpret_cast<uint4*>(dst + (r >> 3) * (K * 16) + c * 128 + (r & 7) * 16) = src[i];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    unsigned char* act = fz_smem + N.a_off;
+    uint32_t phase = 0u;
+    bool ok = true;
+    const int64_t tiles = (n + 127) / 128;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int64_t row = t * 128 + rt;  // this thread's row = its tensor-memory lane
+        if (grp == 0) {
+            // the row's inputs, normalised, as BF16 (K = in_p of layer 0)
+            const int K = N.in_p[0];
+            for (int c0 = 0; c0 < K; c0 += 8) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = c0 + j;
+                    v[j] = (row < n && c < N.n_in) ? (X[row * N.n_in + c] - norm[c]) / norm[16 + c] : 0.f;
+                }
+                *reinterpret_cast<uint4*>(act + (rt >> 3) * (K * 16) + (c0 >> 3) * 128 + (rt & 7) * 16) =
+                    pack_bf16x8(v);
+            }
+        }
+        for (int l = 0; l < N.n_layers; ++l) {
+            const int K = N.in_p[l], Nn = N.out_p[l];
+            const bool last = l == N.n_layers - 1;
+            // the activations written by the threads must be visible to the
+            // tensor core's (async proxy) reads, and every warp done reading
+            // the accumulator of the previous layer
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t idesc = tc_idesc(128, Nn);
+                const uint32_t a0 = smem_u32(act), b0 = smem_u32(fz_smem + N.w_off[l]);
+                const uint32_t sbo = (uint32_t)K * 16u;
+                for (int s = 0; s < (K >> 4); ++s) {
+                    const uint64_t da = tc_sdesc(a0 + 256u * s, 128u, sbo);
+                    const uint64_t db = tc_sdesc(b0 + 256u * s, 128u, sbo);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar0)
+                             : "memory");
+            }
+            ok = __syncthreads_and(mbar_wait(bar0, phase)) != 0;
+            if (!ok) break;  // block-uniform
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const float* bias = N.b[l];
+            for (int c0 = 16 * grp; c0 < Nn; c0 += 16 * kFzGroups) {
+                uint32_t r[16];
+                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                    : "r"(ta)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + bias[c0 + j];
+                if (!last) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = silu(v[j]);
+                    // the next layer's K is this layer's out_p
+                    unsigned char* d = act + (rt >> 3) * (Nn * 16) + (c0 >> 3) * 128 + (rt & 7) * 16;
+                    *reinterpret_cast<uint4*>(d) = pack_bf16x8(v);
+                    *reinterpret_cast<uint4*>(d + 128) = pack_bf16x8(v + 8);
+                } else if (row < n) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = c0 + j;
+                        if (c < N.n_out) Y[row * N.n_out + c] = v[j] * norm[48 + c] + norm[32 + c];
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // the MMAs of the expired wait may still be running: wait again
+        // (bounded) before the tensor memory is given back
+        (void)__syncthreads_and(mbar_wait(bar0, phase));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(N.ncols) : "memory");
+    }
+}
+
+// shared memory above which the fused kernel is not used (one CTA per SM)
+constexpr size_t kFusedMaxSmem = 200 * 1024;
+
 // C[M][N] = A[M][K] . B[N][K]^T; M % 16 == 0, 16 <= N <= 256 with N % 16 == 0,
 // K % 16 == 0.  Tiles of 128 rows x BN columns; narrower column tiles and a
 // split of K (partial sums added atomically into z) when there are too few
@@ -603,6 +779,38 @@ emc_status check_device(emc_mlp* m)
     return EMC_OK;
 }
 
+// The fused inference plan: every layer's weights (128-byte aligned) and one
+// 128-row activation tile in shared memory.  False when they do not fit
+// (the layer-by-layer path runs instead).
+bool fused_plan(const emc_mlp* m, FusedNet& f, size_t& smem)
+{
+    size_t off = 0;
+    int maxk = 16, maxn = 16;
+    f.n_layers = m->n_layers;
+    f.n_in = m->cfg.n_in;
+    f.n_out = m->cfg.n_out;
+    for (int l = 0; l < m->n_layers; ++l) {
+        const Layer& y = m->L[l];
+        f.W[l] = y.Wb;
+        f.b[l] = y.b;
+        f.in_p[l] = y.in_p;
+        f.out_p[l] = y.out_p;
+        f.w_off[l] = (uint32_t)off;
+        off = (off + (size_t)y.out_p * y.in_p * 2 + 127) & ~size_t(127);
+        maxk = std::max(maxk, std::max(y.in_p, y.out_p));
+        maxn = std::max(maxn, y.out_p);
+    }
+    f.a_off = (uint32_t)off;
+    off += (size_t)128 * maxk * 2;
+    uint32_t nc = 32;
+    while (nc < (uint32_t)maxn) nc <<= 1;
+    f.ncols = nc;
+    // no more CTAs may share an SM than its 512 tensor-memory columns hold:
+    // each asks for at least 448 bytes of shared memory per column
+    smem = std::max(off, (size_t)nc * 448);
+    return maxn <= 256 && smem <= kFusedMaxSmem;
+}
+
 int64_t n_params(const emc_mlp* m)
 {
     int64_t n = 0;
@@ -662,6 +870,9 @@ emc_status emc_mlp_create(const emc_mlp_config* cfg, void* stream, emc_mlp** out
     MCK(malloc0(m, &m->loss, 1));
     MCK(malloc0(m, &m->d_err, 1));
     MCK(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcMaxSmem));
+    MCK(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedMaxSmem));
+    MCK(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared));
     emc_status s = refresh_bf16(m);
     if (s != EMC_OK) return s;
     MCK(cudaStreamSynchronize(m->st));
@@ -677,11 +888,51 @@ emc_status emc_mlp_debug_set_error(emc_mlp* m)
     return EMC_OK;
 }
 
+emc_status emc_mlp_set_fused(emc_mlp* m, int32_t enable)
+{
+    if (!m) return EMC_EINVAL;
+    m->fused = enable != 0;
+    return EMC_OK;
+}
+
 emc_status emc_mlp_infer(emc_mlp* m, const float* X, float* Y, int64_t n)
 {
     EMC_TRACE("emc_mlp_infer");
     if (!m || (n > 0 && (!X || !Y)) || n < 0) return EMC_EINVAL;
     if (n == 0) return EMC_OK;
+    FusedNet f{};
+    size_t fsm = 0;
+    if (m->fused && fused_plan(m, f, fsm)) {
+        const int64_t chunk = 1 << 20;
+        const int64_t want = std::min(n, chunk);
+        if (want > m->fcap) {
+            mfree(m, m->fX);
+            mfree(m, m->fY);
+            m->fcap = 0;
+            MCK(malloc0(m, &m->fX, (size_t)want * m->cfg.n_in));
+            MCK(malloc0(m, &m->fY, (size_t)want * m->cfg.n_out));
+            m->fcap = want;
+        }
+        int dev = 0, sms = 0;
+        MCK(cudaGetDevice(&dev));
+        MCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        // two CTAs per SM where they fit (one's epilogue overlaps the other's
+        // MMAs); CTAs beyond what is resident wait for a free slot, and the
+        // shared-memory request keeps the resident ones within the SM's
+        // tensor memory
+        const int per_sm = 2;
+        for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+            const int64_t nn = std::min(chunk, n - r0);
+            MCK(cudaMemcpyAsync(m->fX, X + r0 * m->cfg.n_in, 4 * nn * m->cfg.n_in, cudaMemcpyHostToDevice, m->st));
+            const int64_t tiles = (nn + 127) / 128;
+            const int grid = (int)std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * sms);
+            k_mlp_fused<<<grid, 128 * kFzGroups, fsm, m->st>>>(f, m->fX, nn, m->norm, m->fY, m->d_err);
+            MCK(cudaGetLastError());
+            MCK(cudaMemcpyAsync(Y + r0 * m->cfg.n_out, m->fY, 4 * nn * m->cfg.n_out, cudaMemcpyDeviceToHost, m->st));
+        }
+        MCK(cudaStreamSynchronize(m->st));
+        return check_device(m);
+    }
     const int64_t chunk = 1 << 16;
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t nn = std::min(chunk, n - r0);

@@ -605,8 +605,9 @@ def _mlp_lib():
         L.emc_mlp_last_error.restype = C.c_char_p
         L.emc_mlp_destroy.argtypes = [P]
         L.emc_mlp_debug_set_error.argtypes = [P]
+        L.emc_mlp_set_fused.argtypes = [P, C.c_int32]
         for f in ("emc_mlp_create", "emc_mlp_train", "emc_mlp_infer", "emc_mlp_grad", "emc_mlp_params",
-                  "emc_mlp_debug_set_error"):
+                  "emc_mlp_debug_set_error", "emc_mlp_set_fused"):
             getattr(L, f).restype = C.c_int
         L._mlp_ready = True
     return L
@@ -687,6 +688,11 @@ class Mlp:
         Y = np.zeros((X.shape[0], self.n_out), dtype=np.float32)
         self._check(_mlp_lib().emc_mlp_infer(self.h, _p(X, C.c_float), _p(Y, C.c_float), X.shape[0]))
         return Y
+
+    def set_fused(self, enable: bool = True):
+        """Inference in one fused launch (default, when the network fits) or
+        one launch per layer."""
+        self._check(_mlp_lib().emc_mlp_set_fused(self.h, int(bool(enable))))
 
     def debug_set_error(self):
         """Set the device error word as an expired tensor-core wait would."""

@@ -160,3 +160,25 @@ def test_expired_wait_is_reported_and_the_handle_recovers(emc):
         net.infer(X)
     assert ei.value.status == 5 and "expired" in str(ei.value)
     np.testing.assert_array_equal(net.infer(X), want)
+
+
+@pytest.mark.parametrize("n_in,hidden,layers,n_out,rows", [(4, 128, 3, 7, 115_200), (4, 128, 3, 7, 1),
+                                                           (16, 48, 2, 16, 1000), (3, 256, 1, 5, 333),
+                                                           (5, 16, 6, 2, 129)])
+def test_fused_inference_equals_layer_by_layer(emc, n_in, hidden, layers, n_out, rows):
+    """The fused inference (every layer in one launch, weights and one
+    activation tile in shared memory) against the layer-by-layer GEMM path
+    on the same weights (the same normalisation, BF16 operands, MMA order,
+    FP32 bias and SiLU): equal to FP32 rounding, ragged tiles included, and
+    both against the FP64 reference network."""
+    net, nrm, sizes, rng = make(emc, n_in=n_in, hidden=hidden, layers=layers, n_out=n_out, seed=17)
+    X = rng.normal(size=(rows, n_in)).astype(np.float32)
+    fused = net.infer(X)
+    net.set_fused(False)
+    layered = net.infer(X)
+    net.set_fused(True)
+    scale = np.abs(layered - nrm["y_shift"]).max()
+    np.testing.assert_allclose(fused, layered, rtol=0, atol=1e-5 * scale)
+    idx = rng.choice(rows, min(rows, 2000), replace=False)
+    want = ref.predict(net.params().astype(np.float64), sizes, X[idx], nrm)
+    assert np.abs(fused[idx] - want).max() / np.abs(want - nrm["y_shift"]).max() < 3e-2

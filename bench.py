@@ -566,8 +566,10 @@ def phonon_comparison(args, stream) -> dict:
         # the coupled fixed points from 300 K: electrons <-> phonon Monte
         # Carlo, and electrons <-> Fourier (the same electron windows)
         T0 = np.full((1, ctx.n_cell), 300.0)
-        hy = ET.hybrid_iterate(ctx, tc, pc, T0, args.phonon_loop_bundles, max_iter=10, first=10 * N)
-        fo = ET.iterate(ctx, tc_f, T0, max_iter=10)
+        # 3000-step averaging windows: the half-window noise of one wire's
+        # hot spot with 1000 steps (~20 K) let a loop stop a step early
+        hy = ET.hybrid_iterate(ctx, tc, pc, T0, args.phonon_loop_bundles, avg_steps=3000, max_iter=10, first=10 * N)
+        fo = ET.iterate(ctx, tc_f, T0, avg_steps=3000, max_iter=10)
     finally:
         ctx.close()
     P = r["power_W"]
@@ -598,7 +600,7 @@ def phonon_comparison(args, stream) -> dict:
         "peak_rise_K": {"phonon_mc": peak_mc, "fourier": peak_f, "mc_passes": mc["peak_history"]},
         "R_th_K_per_W_half_wire": {"phonon_mc": peak_mc / net, "fourier": peak_f / net},
         "coupled_fixed_point": {
-            "what": "electron MC <-> phonon MC and electron MC <-> Fourier from 300 K (300 + 1000 steps per "
+            "what": "electron MC <-> phonon MC and electron MC <-> Fourier from 300 K (300 + 3000 steps per "
                     "iteration, %d bundles per phonon solve); stop: every subcell within max(0.1 K, the noise)"
                     % args.phonon_loop_bundles,
             "phonon_mc": {"converged": bool(hy["converged"]), "iterations": int(hy["iterations"]),

@@ -97,7 +97,9 @@ int pad16(int x) { return (x + 15) / 16 * 16; }
 unsigned gridn(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ------------------------------------------------------------- tensor core
-__device__ __forceinline__ float silu(float x) { return x / (1.f + __expf(-x)); }
+// x sigmoid(x) with the hardware exponential and the approximate division
+// (for x below about -88 the denominator is infinite and the result 0)
+__device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.f + __expf(-x)); }
 __device__ __forceinline__ float dsilu(float x)
 {
     const float s = 1.f / (1.f + __expf(-x));
